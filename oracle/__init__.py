@@ -1,0 +1,225 @@
+"""ORACLE -- test infrastructure only.
+
+Plain CPU statement of the temporal path queries (earliest arrival, latest departure),
+used by the test suite, the package smoke check and the CPU-baseline leg of the
+benchmark, and by nothing in the library.  `oracle.c` holds the single-threaded one-pass
+scans; this module loads it and adds pure-Python brute force over simple paths for tiny
+graphs.  It shares no code with the CUDA library and imports only numpy and ctypes; edge
+lists are passed in as any object with n, src, dst, t and lam attributes.
+
+Semantics (the paper's Sec. 2.1 edge model, Sec. 2.2 ordering predicates, Alg. 2 as read
+with the source initialised to the window start):
+  * edge (u, v, t, lam) departs u at t, arrives at v at t + lam;
+  * window [ta, tw] inclusive: usable edges have t >= ta and t + lam <= tw;
+  * consecutive edges e, f of a path: t_f >= t_e + lam_e (Succeeds) or > (StrictlySucceeds);
+    the first edge may depart at ta and the last may arrive at tw under either predicate;
+  * EA[s] = ta; EA[v] = min arrival over paths s -> v; LD[x] = tw; LD[u] = max first
+    departure over paths u -> x; unreachable = 0xFFFFFFFF.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+UNREACHED = 0xFFFFFFFF
+C_MIRROR = 0xFFFFFFFE
+_P = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc -O2, plain C)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.oracle_time_order.argtypes = [ctypes.c_int64, _P, _P]
+        L.oracle_time_order.restype = ctypes.c_int
+        for fn in ("oracle_earliest_arrival", "oracle_latest_departure"):
+            f = getattr(L, fn)
+            f.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int32,
+                          ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _P]
+            f.restype = ctypes.c_int
+        L.oracle_admissible_ea.argtypes = [ctypes.c_int64, _P, _P, _P, _P, ctypes.c_int32,
+                                           ctypes.c_uint32, ctypes.c_int]
+        L.oracle_admissible_ea.restype = ctypes.c_uint64
+        L.oracle_admissible_ld.argtypes = [ctypes.c_int64, _P, _P, _P, _P, ctypes.c_int32,
+                                           ctypes.c_uint32, ctypes.c_int]
+        L.oracle_admissible_ld.restype = ctypes.c_uint64
+        L.oracle_certify_ea.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_int32,
+                                        ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _P,
+                                        ctypes.POINTER(ctypes.c_int64)]
+        L.oracle_certify_ea.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _arrays(el):
+    src = np.ascontiguousarray(el.src, np.int32)
+    dst = np.ascontiguousarray(el.dst, np.int32)
+    t = np.ascontiguousarray(el.t, np.uint32)
+    lam = np.ascontiguousarray(el.lam, np.uint32)  # widened copy when durations are uint16
+    return src, dst, t, lam
+
+
+class Oracle:
+    """The oracle bound to one edge list: sorts it by departure time once (qsort), then
+    answers queries by the one-pass scans of oracle.c."""
+
+    def __init__(self, el):
+        self.n = int(el.n)
+        self.src, self.dst, self.t, self.lam = _arrays(el)
+        self.m = int(self.src.shape[0])
+        self.perm = np.empty(self.m, np.uint32)
+        L = _load()
+        if L.oracle_time_order(self.m, self.t.ctypes.data, self.perm.ctypes.data) != 0:
+            raise MemoryError("oracle_time_order failed")
+
+    def _ptrs(self):
+        return (self.src.ctypes.data, self.dst.ctypes.data, self.t.ctypes.data,
+                self.lam.ctypes.data, self.perm.ctypes.data)
+
+    def earliest_arrival(self, s: int, ta: int, tw: int, strict: int = 0) -> np.ndarray:
+        out = np.empty(self.n, np.uint32)
+        rc = _load().oracle_earliest_arrival(self.n, self.m, *self._ptrs(), int(s), int(ta), int(tw),
+                                             int(strict), out.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle_earliest_arrival: invalid arguments")
+        return out
+
+    def latest_departure(self, x: int, ta: int, tw: int, strict: int = 0) -> np.ndarray:
+        out = np.empty(self.n, np.uint32)
+        rc = _load().oracle_latest_departure(self.n, self.m, *self._ptrs(), int(x), int(ta), int(tw),
+                                             int(strict), out.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle_latest_departure: invalid arguments")
+        return out
+
+    def query(self, q) -> np.ndarray:
+        """q has .kind (0 EA, 1 LD), .vertex, .ta, .tw, .strict."""
+        if q.kind == 0:
+            return self.earliest_arrival(q.vertex, q.ta, q.tw, q.strict)
+        return self.latest_departure(q.vertex, q.ta, q.tw, q.strict)
+
+    def admissible(self, q, labels: np.ndarray) -> int:
+        """TE(q): edges usable under the final labels of query q."""
+        labels = np.ascontiguousarray(labels, np.uint32)
+        L = _load()
+        if q.kind == 0:
+            return int(L.oracle_admissible_ea(self.m, self.src.ctypes.data, self.t.ctypes.data,
+                                              self.lam.ctypes.data, labels.ctypes.data, int(q.vertex),
+                                              int(q.tw), int(q.strict)))
+        return int(L.oracle_admissible_ld(self.m, self.dst.ctypes.data, self.t.ctypes.data,
+                                          self.lam.ctypes.data, labels.ctypes.data, int(q.vertex),
+                                          int(q.ta), int(q.strict)))
+
+
+def certify_ea(el, s: int, ta: int, tw: int, strict: int, labels: np.ndarray):
+    """Certificate check of earliest-arrival labels at any size (see oracle.c).
+    Returns (status, bad): 0 holds, 1 fails at `bad`, 2 not applicable (lam == 0, Succeeds)."""
+    src, dst, t, lam = _arrays(el)
+    labels = np.ascontiguousarray(labels, np.uint32)
+    bad = ctypes.c_int64(0)
+    rc = _load().oracle_certify_ea(int(el.n), int(src.shape[0]), src.ctypes.data, dst.ctypes.data,
+                                   t.ctypes.data, lam.ctypes.data, int(s), int(ta), int(tw), int(strict),
+                                   labels.ctypes.data, ctypes.byref(bad))
+    if rc < 0:
+        raise ValueError("oracle_certify_ea: invalid arguments")
+    return rc, int(bad.value)
+
+
+def mirror_edges(src, dst, t, lam):
+    """Reverse, time-mirrored edge list: (v, u, C - (t + lam), lam).  A path u -> x that
+    departs at t1 maps to a path x -> u arriving at C - t1, so latest departure in [ta, tw]
+    equals C minus earliest arrival on the mirror in [C - tw, C - ta]."""
+    t2 = (np.uint64(C_MIRROR) - (t.astype(np.uint64) + lam.astype(np.uint64))).astype(np.uint32)
+    return dst.copy(), src.copy(), t2, lam.astype(np.uint32)
+
+
+# ---- brute force over simple paths (pure Python, tiny graphs only) ---------------------
+
+def _usable(t, lam, ta, tw):
+    return t >= ta and t + lam <= tw
+
+
+def brute_earliest_arrival(n, src, dst, t, lam, s, ta, tw, strict=0, used=None):
+    """Enumerate every vertex-simple time-respecting path from s (a cycle can always be cut
+    out of a time-respecting walk without delaying its end) and keep the minimum arrival.
+    If `used` is a set, it receives every edge that can extend some such path."""
+    out = [UNREACHED] * n
+    out[s] = ta
+    adj = [[] for _ in range(n)]
+    for e in range(len(src)):
+        adj[int(src[e])].append(e)
+
+    def go(u, arrival, first, onpath):
+        for e in adj[u]:
+            te, le = int(t[e]), int(lam[e])
+            if not _usable(te, le, ta, tw):
+                continue
+            if not first and (te <= arrival if strict else te < arrival):
+                continue
+            if used is not None:
+                used.add(e)
+            v = int(dst[e])
+            if v in onpath:
+                continue
+            if te + le < out[v]:
+                out[v] = te + le
+            onpath.add(v)
+            go(v, te + le, False, onpath)
+            onpath.discard(v)
+
+    go(s, ta, True, {s})
+    return np.array(out, np.uint32)
+
+
+def brute_latest_departure(n, src, dst, t, lam, x, ta, tw, strict=0, used=None):
+    """Enumerate every vertex-simple time-respecting path into x, walking backwards, and
+    keep the maximum first departure per start vertex.  If `used` is a set, it receives
+    every edge that can precede some such path."""
+    out = [UNREACHED] * n
+    out[x] = tw
+    radj = [[] for _ in range(n)]
+    for e in range(len(src)):
+        radj[int(dst[e])].append(e)
+
+    def go(v, bound, last, onpath):
+        # bound: departure time of the path's next edge out of v (tw when v is the target)
+        for e in radj[v]:
+            te, le = int(t[e]), int(lam[e])
+            if not _usable(te, le, ta, tw):
+                continue
+            if not last and (te + le >= bound if strict else te + le > bound):
+                continue
+            if used is not None:
+                used.add(e)
+            u = int(src[e])
+            if u in onpath:
+                continue
+            if out[u] == UNREACHED or te > out[u]:
+                out[u] = te
+            onpath.add(u)
+            go(u, te, False, onpath)
+            onpath.discard(u)
+
+    go(x, tw, True, {x})
+    return np.array(out, np.uint32)

@@ -1,0 +1,225 @@
+/*
+ * ORACLE -- test infrastructure only.
+ *
+ * A plain, slow, single-threaded CPU statement of the temporal path queries that the GPU
+ * library answers.  Only the test suite, the smoke check of the package entry point and
+ * the CPU-baseline leg of the benchmark load this file; the library never does, and the
+ * two share no code.
+ *
+ * Model (Sec. 2.1): discrete time; an edge (u, v, t, lam) is valid on [t, t + lam], i.e.
+ * it departs u at t and arrives at v at t + lam.  All arithmetic is exact uint32.
+ * Ordering predicates (Sec. 2.2): consecutive edges A then B form a path when
+ * end(A) <= start(B) ("Succeeds", strict = 0) or end(A) < start(B) ("StrictlySucceeds",
+ * strict = 1).
+ * Window [ta, tw], inclusive at both ends: an edge is usable when t >= ta and
+ * t + lam <= tw (the window test of the Update function of Alg. 2, with its first
+ * comparison read as "reject t < ta").  The ordering predicate relates consecutive edges
+ * only: the first edge of a path may depart at exactly ta and the last may arrive at
+ * exactly tw under either predicate.
+ *
+ * Earliest arrival from s (Alg. 2, read with the source s initialised to ta and the
+ * frontier as the set of improved vertices): ea[s] = ta, and for v != s the minimum
+ * arrival time over time-respecting paths from s in the window; UNREACHED (0xFFFFFFFF)
+ * otherwise.  Latest departure to x (a "minimal temporal path" of Sec. 2.3, defined by
+ * the paper's reference on temporal path problems): ld[x] = tw, and for u != x the
+ * maximum first departure time over time-respecting paths from u to x in the window;
+ * UNREACHED otherwise.
+ *
+ * Algorithm: the one-pass scan over the time-ordered edge stream of that reference
+ * (credited in Sec. 7): edges are visited in ascending t (descending for latest
+ * departure), and every edge sharing the same t is re-swept until nothing changes, which
+ * only matters when a zero-duration edge under Succeeds can enable another edge of the
+ * same instant.  The sort is the C library's qsort.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+
+#define UNREACHED 0xFFFFFFFFu
+
+static int cmp_u64(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* perm[k] = index of the k-th edge in ascending departure time (ties by edge index).
+ * Requires m < 2^32.  Returns 0, or -1 on bad arguments / allocation failure. */
+int oracle_time_order(int64_t m, const uint32_t *t, uint32_t *perm) {
+    if (m < 0 || m > (int64_t)0xFFFFFFFFLL || (m > 0 && (!t || !perm))) return -1;
+    uint64_t *key = (uint64_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(uint64_t));
+    if (!key) return -1;
+    for (int64_t i = 0; i < m; ++i) key[i] = ((uint64_t)t[i] << 32) | (uint64_t)i;
+    qsort(key, (size_t)m, sizeof(uint64_t), cmp_u64);
+    for (int64_t i = 0; i < m; ++i) perm[i] = (uint32_t)(key[i] & 0xFFFFFFFFu);
+    free(key);
+    return 0;
+}
+
+static int check_common(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                        const uint32_t *lam, const uint32_t *perm, int32_t vtx, uint32_t ta, uint32_t tw,
+                        const uint32_t *out) {
+    if (n <= 0 || m < 0 || vtx < 0 || vtx >= n || ta > tw || tw > 0xFFFFFFFEu || !out) return -1;
+    if (m > 0 && (!src || !dst || !t || !lam || !perm)) return -1;
+    return 0;
+}
+
+/* Earliest arrival from s within [ta, tw]; out[n]. */
+int oracle_earliest_arrival(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                            const uint32_t *lam, const uint32_t *perm, int32_t s, uint32_t ta, uint32_t tw,
+                            int strict, uint32_t *out) {
+    if (check_common(n, m, src, dst, t, lam, perm, s, ta, tw, out)) return -1;
+    for (int64_t v = 0; v < n; ++v) out[v] = UNREACHED;
+    out[s] = ta;
+    int64_t k = 0;
+    while (k < m && t[perm[k]] < ta) ++k; /* edges departing before the window */
+    while (k < m && t[perm[k]] <= tw) {
+        uint32_t now = t[perm[k]];
+        int64_t end = k;
+        while (end < m && t[perm[end]] == now) ++end; /* the group of edges departing at `now` */
+        int again = 1;
+        while (again) {
+            again = 0;
+            for (int64_t j = k; j < end; ++j) {
+                uint32_t e = perm[j];
+                uint32_t au = out[src[e]];
+                if (au == UNREACHED) continue;                  /* u not reached yet */
+                int first = (src[e] == s);                       /* leaves the source */
+                if ((strict && !first) ? !(au < now) : !(au <= now)) continue; /* predicate */
+                uint64_t arrive = (uint64_t)now + lam[e];
+                if (arrive > tw) continue;                      /* leaves the window */
+                if (arrive < out[dst[e]]) {
+                    out[dst[e]] = (uint32_t)arrive;
+                    if (arrive == now && !strict) again = 1;    /* may enable this instant */
+                }
+            }
+        }
+        k = end;
+    }
+    return 0;
+}
+
+/* Latest departure towards x within [ta, tw]; out[n]. */
+int oracle_latest_departure(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                            const uint32_t *lam, const uint32_t *perm, int32_t x, uint32_t ta, uint32_t tw,
+                            int strict, uint32_t *out) {
+    if (check_common(n, m, src, dst, t, lam, perm, x, ta, tw, out)) return -1;
+    for (int64_t v = 0; v < n; ++v) out[v] = UNREACHED;
+    out[x] = tw;
+    int64_t k = m - 1;
+    while (k >= 0 && t[perm[k]] > tw) --k; /* edges departing after the window */
+    while (k >= 0 && t[perm[k]] >= ta) {
+        uint32_t now = t[perm[k]];
+        int64_t beg = k;
+        int has_zero = 0; /* a zero-duration edge of this instant can follow a new label */
+        while (beg >= 0 && t[perm[beg]] == now) has_zero |= (lam[perm[beg--]] == 0);
+        /* the group is perm[beg+1 .. k] */
+        int again = 1;
+        while (again) {
+            again = 0;
+            for (int64_t j = k; j > beg; --j) {
+                uint32_t e = perm[j];
+                uint32_t lv = out[dst[e]];
+                if (lv == UNREACHED) continue;                    /* v cannot reach x */
+                uint64_t arrive = (uint64_t)now + lam[e];
+                if (arrive > tw) continue;                        /* leaves the window */
+                int last = (dst[e] == x);                          /* enters the target */
+                if ((strict && !last) ? !(arrive < lv) : !(arrive <= lv)) continue; /* predicate */
+                uint32_t lu = out[src[e]];
+                if (lu == UNREACHED || now > lu) {
+                    out[src[e]] = now; /* u can now be entered by a lam = 0 edge at `now` */
+                    if (has_zero && !strict) again = 1;
+                }
+            }
+        }
+        k = beg;
+    }
+    return 0;
+}
+
+/* Number of edges usable under final earliest-arrival labels from s: ea[u] reached,
+ * t >= ea[u] (> when strict and u != s) and t + lam <= tw.  (t >= ta follows from
+ * ea[u] >= ta.) */
+uint64_t oracle_admissible_ea(int64_t m, const int32_t *src, const uint32_t *t, const uint32_t *lam,
+                              const uint32_t *ea, int32_t s, uint32_t tw, int strict) {
+    uint64_t c = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        uint32_t au = ea[src[e]];
+        if (au == UNREACHED) continue;
+        if ((strict && src[e] != s) ? !(au < t[e]) : !(au <= t[e])) continue;
+        if ((uint64_t)t[e] + lam[e] > tw) continue;
+        ++c;
+    }
+    return c;
+}
+
+/* Number of edges usable under final latest-departure labels towards x: ld[v] reached,
+ * t + lam <= ld[v] (< when strict and v != x) and t >= ta.  (t + lam <= tw follows from
+ * ld[v] <= tw.) */
+uint64_t oracle_admissible_ld(int64_t m, const int32_t *dst, const uint32_t *t, const uint32_t *lam,
+                              const uint32_t *ld, int32_t x, uint32_t ta, int strict) {
+    uint64_t c = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        uint32_t lv = ld[dst[e]];
+        if (lv == UNREACHED) continue;
+        uint64_t arrive = (uint64_t)t[e] + lam[e];
+        if ((strict && dst[e] != x) ? !(arrive < lv) : !(arrive <= lv)) continue;
+        if (t[e] < ta) continue;
+        ++c;
+    }
+    return c;
+}
+
+/*
+ * Certificate check of a claimed earliest-arrival labelling `ea` at any size, in one pass
+ * over the unsorted edges (no sort, O(n + m)).  It holds exactly when `ea` equals the
+ * definition above, provided every duration is >= 1 or strict = 1 (then every witness
+ * chain strictly decreases in time and ends at s):
+ *   (1) ea[s] = ta, and every other reached label lies in (ta, tw];
+ *   (2) closure: no usable edge improves a label (ea[u] reached, t >= ea[u] (> when
+ *       strict and u != s), t + lam <= tw  =>  ea[v] <= t + lam);
+ *   (3) witness: every reached v != s has a usable edge with t + lam == ea[v].
+ * (2) gives ea <= EA along every path; (3) with strictly decreasing witness chains gives
+ * ea >= EA.  Returns 0 when the certificate holds, 1 when it fails (first offending
+ * vertex or edge index in *bad, negative for edges: -(e+1)), -1 on bad arguments,
+ * 2 when it does not apply (some lam == 0 with strict == 0).
+ */
+int oracle_certify_ea(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                      const uint32_t *lam, int32_t s, uint32_t ta, uint32_t tw, int strict,
+                      const uint32_t *ea, int64_t *bad) {
+    if (n <= 0 || m < 0 || s < 0 || s >= n || ta > tw || !ea || !bad) return -1;
+    *bad = 0;
+    if (!strict)
+        for (int64_t e = 0; e < m; ++e)
+            if (lam[e] == 0) return 2;
+    if (ea[s] != ta) {
+        *bad = s;
+        return 1;
+    }
+    for (int64_t v = 0; v < n; ++v)
+        if (v != s && ea[v] != UNREACHED && !(ea[v] > ta && ea[v] <= tw)) {
+            *bad = v;
+            return 1;
+        }
+    unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
+    if (!seen) return -1;
+    for (int64_t e = 0; e < m; ++e) {
+        uint32_t au = ea[src[e]];
+        if (au == UNREACHED) continue;
+        if ((strict && src[e] != s) ? !(au < t[e]) : !(au <= t[e])) continue;
+        uint64_t arrive = (uint64_t)t[e] + lam[e];
+        if (arrive > tw) continue;
+        if ((uint64_t)ea[dst[e]] > arrive) { /* closure violated */
+            free(seen);
+            *bad = -(e + 1);
+            return 1;
+        }
+        if ((uint64_t)ea[dst[e]] == arrive) seen[dst[e]] = 1;
+    }
+    for (int64_t v = 0; v < n; ++v)
+        if (v != s && ea[v] != UNREACHED && !seen[v]) { /* no witness */
+            free(seen);
+            *bad = v;
+            return 1;
+        }
+    free(seen);
+    return 0;
+}

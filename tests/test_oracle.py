@@ -1,0 +1,219 @@
+"""Pins for the oracle, checked against things other than itself: a hand-worked example,
+brute force over simple paths, textbook reductions, the mirror identity between the two
+query kinds, and invariants that the definitions fix.  CPU only."""
+import json
+import os
+from collections import deque
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import (C_MIRROR, UNREACHED, Oracle, brute_earliest_arrival, brute_latest_departure,
+                    certify_ea, mirror_edges)
+from synth import EA, LD, Query
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+class Edges:
+    def __init__(self, n, src, dst, t, lam):
+        self.n = n
+        self.src = np.asarray(src, np.int32)
+        self.dst = np.asarray(dst, np.int32)
+        self.t = np.asarray(t, np.uint32)
+        self.lam = np.asarray(lam, np.uint32)
+
+
+def from_rows(n, rows):
+    r = np.array(rows, dtype=np.int64).reshape(-1, 4)
+    return Edges(n, r[:, 0], r[:, 1], r[:, 2], r[:, 3])
+
+
+def test_hand_worked_example():
+    g = json.load(open(os.path.join(HERE, "golden", "hand_example.json")))
+    el = from_rows(g["n"], g["edges_u_v_t_lam"])
+    orc = Oracle(el)
+    for c in g["cases"]:
+        q = Query(EA if c["kind"] == "EA" else LD, c["vertex"], c["ta"], c["tw"], c["strict"])
+        got = orc.query(q)
+        assert got.tolist() == c["expect"], c
+        brute = (brute_earliest_arrival if q.kind == EA else brute_latest_departure)(
+            el.n, el.src, el.dst, el.t, el.lam, q.vertex, q.ta, q.tw, q.strict)
+        assert brute.tolist() == c["expect"], c
+        if "admissible" in c:
+            assert orc.admissible(q, got) == c["admissible"]
+
+
+def _tiny_cases(count):
+    for seed in range(count):
+        n = 2 + seed % 7
+        m = 1 + (seed * 7) % 18
+        el = synth.random_small(n, m, 0x7100 + seed, t_max=6, lam_max=3, lam_min=0)
+        d = lambda k: synth.draw(0x7200 + seed, 0, k)
+        v = synth.below(d(0), n)
+        ta = synth.below(d(1), 4)
+        tw = ta + synth.below(d(2), 8)
+        yield el, v, ta, tw
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_brute_force_tiny_graphs(strict):
+    """Thousands of tiny multigraphs with self-loops, parallel edges and zero durations."""
+    checked = 0
+    for el, v, ta, tw in _tiny_cases(1500):
+        orc = Oracle(el)
+        used = set()
+        want = brute_earliest_arrival(el.n, el.src, el.dst, el.t, el.lam, v, ta, tw, strict, used)
+        got = orc.earliest_arrival(v, ta, tw, strict)
+        assert np.array_equal(got, want), (el.src, el.dst, el.t, el.lam, v, ta, tw)
+        assert orc.admissible(Query(EA, v, ta, tw, strict), got) == len(used)
+        used = set()
+        want = brute_latest_departure(el.n, el.src, el.dst, el.t, el.lam, v, ta, tw, strict, used)
+        got = orc.latest_departure(v, ta, tw, strict)
+        assert np.array_equal(got, want), (el.src, el.dst, el.t, el.lam, v, ta, tw)
+        assert orc.admissible(Query(LD, v, ta, tw, strict), got) == len(used)
+        checked += 1
+    assert checked == 1500
+
+
+def _bfs(n, src, dst, s):
+    adj = [[] for _ in range(n)]
+    for u, v in zip(src, dst):
+        adj[int(u)].append(int(v))
+    dist = [-1] * n
+    dist[s] = 0
+    dq = deque([s])
+    while dq:
+        u = dq.popleft()
+        for v in adj[u]:
+            if dist[v] < 0:
+                dist[v] = dist[u] + 1
+                dq.append(v)
+    return dist
+
+
+def test_reduction_static_reachability():
+    """Every edge at t = 0 with zero duration: earliest arrival reaches exactly the
+    vertices BFS reaches, all at time 0."""
+    for seed in range(20):
+        el = synth.random_small(40, 90, 0x7300 + seed, t_max=0, lam_max=0)
+        s = seed % 40
+        got = Oracle(el).earliest_arrival(s, 0, 5)
+        dist = _bfs(el.n, el.src, el.dst, s)
+        assert [g == 0 for g in got] == [d >= 0 for d in dist]
+        assert all(g in (0, UNREACHED) for g in got)
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_reduction_hop_distance(strict):
+    """A static graph whose every edge is present at each integer time 0..H with duration 1:
+    earliest arrival from s at time 0 is the BFS hop distance d (Succeeds), or 2d - 1
+    (StrictlySucceeds: every later hop must wait one more instant)."""
+    H = 12
+    for seed in range(10):
+        st = synth.random_small(30, 45, 0x7400 + seed, t_max=0, lam_max=0)
+        rows = [(int(u), int(v), tt, 1) for u, v in zip(st.src, st.dst) for tt in range(H + 1)]
+        el = from_rows(30, rows)
+        s = seed
+        got = Oracle(el).earliest_arrival(s, 0, H + 1, strict)
+        dist = _bfs(30, st.src, st.dst, s)
+        for v in range(30):
+            d = dist[v]
+            want = 0 if v == s else (UNREACHED if d < 0 else (d if not strict else 2 * d - 1))
+            if want != UNREACHED and want > H + 1:
+                want = UNREACHED
+            assert got[v] == want, (v, d)
+
+
+@pytest.fixture(scope="module")
+def tiny_workload():
+    el = synth.rmat(synth.WORKLOADS[1].graph)
+    return el, Oracle(el)
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_latest_departure_equals_mirrored_earliest_arrival(tiny_workload, strict):
+    """Two independent routes to latest departure: the direct descending scan, and C minus
+    earliest arrival on the reversed, time-mirrored graph over [C - tw, C - ta]."""
+    el, orc = tiny_workload
+    ms, md, mt, ml = mirror_edges(el.src, el.dst, el.t, el.lam)
+    morc = Oracle(Edges(el.n, ms, md, mt, ml))
+    xs = synth.pick_vertices(el, 6, 0x7500 + strict, False, True)
+    for k, x in enumerate(xs):
+        ta, tw = [(0, C_MIRROR), (1000, 900_000), (300_000, 700_000)][k % 3]
+        ld = orc.latest_departure(x, ta, tw, strict)
+        ea = morc.earliest_arrival(x, C_MIRROR - tw, C_MIRROR - ta, strict)
+        back = np.where(ea == UNREACHED, UNREACHED, np.uint32(C_MIRROR) - ea).astype(np.uint32)
+        assert np.array_equal(ld, back)
+        assert orc.admissible(Query(LD, x, ta, tw, strict), ld) == \
+            morc.admissible(Query(EA, x, C_MIRROR - tw, C_MIRROR - ta, strict), ea)
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_invariants_tiny_workload(tiny_workload, strict):
+    el, orc = tiny_workload
+    srcs = synth.pick_vertices(el, 5, 0x7600 + strict, True, False)
+    for s in srcs:
+        ea = orc.earliest_arrival(s, 0, (1 << 20) - 1, strict)
+        assert ea[s] == 0
+        assert certify_ea(el, s, 0, (1 << 20) - 1, strict, ea) == (0, 0)
+        # window extension: labels finite under a narrower end stay equal; new ones exceed it
+        for tw1 in (200_000, 600_000):
+            e1 = orc.earliest_arrival(s, 0, tw1, strict)
+            fin = e1 != UNREACHED
+            assert np.array_equal(e1[fin], ea[fin])
+            assert np.all(ea[~fin & (ea != UNREACHED)] > tw1)
+        # later window start never helps (for v != s)
+        e_late = orc.earliest_arrival(s, 100_000, (1 << 20) - 1, strict)
+        mask = np.arange(el.n) != s
+        assert np.all(ea[mask].astype(np.uint64) <= e_late[mask].astype(np.uint64))
+        # mirrored statements for latest departure: a later window end never hurts
+        ld = orc.latest_departure(s, 0, 600_000, strict)
+        ld2 = orc.latest_departure(s, 0, 900_000, strict)
+        both = (ld != UNREACHED) & mask
+        assert np.all(ld2[both] >= ld[both])
+        assert np.all(ld2[mask & (ld != UNREACHED)] != UNREACHED)
+
+
+def test_certificate_rejects_planted_mistakes(tiny_workload):
+    """The any-size certificate accepts the oracle's labels and rejects each kind of
+    single-label mistake."""
+    el, orc = tiny_workload
+    s = synth.pick_vertices(el, 1, 0x7700, True, False)[0]
+    tw = (1 << 20) - 1
+    ea = orc.earliest_arrival(s, 0, tw, 0)
+    assert certify_ea(el, s, 0, tw, 0, ea)[0] == 0
+    reached = np.flatnonzero((ea != UNREACHED) & (np.arange(el.n) != s))
+    unreached = np.flatnonzero(ea == UNREACHED)
+    assert reached.size > 10 and unreached.size > 0
+    v = int(reached[reached.size // 2])
+    for bad in (ea[v] + 1, ea[v] - 1, UNREACHED):
+        x = ea.copy()
+        x[v] = bad
+        assert certify_ea(el, s, 0, tw, 0, x)[0] == 1, bad
+    x = ea.copy()
+    x[int(unreached[0])] = tw
+    assert certify_ea(el, s, 0, tw, 0, x)[0] == 1
+    x = ea.copy()
+    x[s] = 1
+    assert certify_ea(el, s, 0, tw, 0, x)[0] == 1
+
+
+def test_invalid_arguments_rejected():
+    el = from_rows(3, [(0, 1, 1, 1)])
+    orc = Oracle(el)
+    with pytest.raises(ValueError):
+        orc.earliest_arrival(3, 0, 5)
+    with pytest.raises(ValueError):
+        orc.earliest_arrival(0, 6, 5)
+    with pytest.raises(ValueError):
+        orc.latest_departure(0, 0, 0xFFFFFFFF)
+
+
+def test_empty_graph_and_isolated_source():
+    el = Edges(4, [], [], [], [])
+    orc = Oracle(el)
+    assert orc.earliest_arrival(2, 3, 9).tolist() == [UNREACHED, UNREACHED, 3, UNREACHED]
+    assert orc.latest_departure(1, 3, 9).tolist() == [UNREACHED, 9, UNREACHED, UNREACHED]
