@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark of the temporal edge-map (earliest arrival / latest departure) on GB300.
+
+One step = one batch of the workload's queries answered by the batched persistent
+edge-map on the device-resident graph (64 earliest-arrival + 64 latest-departure queries,
+full window, on the 2^20-vertex, 2^25-edge bursty R-MAT graph with the selective index at
+degree 256).  The graph build (ingest, sort, index) is timed separately.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "GTEPS & % HBM peak, batched vs one-query launch; served queries/s, p50/p99 ms"
+UNIT = "GTEPS"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", type=int, default=2)
+    p.add_argument("--lanes", type=int, default=0, help="0: autotune")
+    p.add_argument("--no-single", action="store_true", help="skip the one-query-per-launch comparison")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.file:
+            return None
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- algorithmic bytes (edge records + atomic words + init/readout) ------------------------
+
+def launch_groups(queries, lanes):
+    """The library's packing: queries grouped by kind in order, `lanes` at a time."""
+    groups = []
+    for kind in (0, 1):
+        idx = [i for i, q in enumerate(queries) if q.kind == kind]
+        groups += [idx[c:c + lanes] for c in range(0, len(idx), lanes)]
+    return groups
+
+
+def union_admissible(torch, E, queries, group, labels_dev):
+    """|union over the group's lanes of the edges usable under the final labels|."""
+    INF = 0xFFFFFFFF
+    anyadm = torch.zeros(E["m"], dtype=torch.bool, device="cuda")
+    for i in group:
+        q = queries[i]
+        lab = labels_dev[i].to(torch.int64) & INF
+        if q.kind == 0:
+            au = lab[E["src"]]
+            thr = au + (q.strict * (E["src"] != q.vertex)).to(torch.int64)
+            adm = (au != INF) & (E["t"] >= thr) & (E["tau"] <= q.tw)
+        else:
+            lv = lab[E["dst"]]
+            lim = lv - (q.strict * (E["dst"] != q.vertex)).to(torch.int64)
+            adm = (lv != INF) & (E["tau"] <= lim) & (E["t"] >= q.ta)
+        anyadm |= adm
+    return int(anyadm.sum().item())
+
+
+def cpu_baseline(el, queries, budget_s=20.0):
+    """The oracle as it stands, single-threaded on a host core, on a bounded sample."""
+    import oracle
+    t0 = time.perf_counter()
+    orc = oracle.Oracle(el)
+    sort_s = time.perf_counter() - t0
+    te = 0
+    scan_s = 0.0
+    done = []
+    order = []
+    half = len(queries) // 2
+    for k in range(half):  # alternate kinds: EA k, LD k
+        order += [k, half + k]
+    for i in order:
+        t1 = time.perf_counter()
+        lab = orc.query(queries[i])
+        scan_s += time.perf_counter() - t1
+        te += orc.admissible(queries[i], lab)
+        done.append(i)
+        if scan_s > budget_s:
+            break
+    return {"value": te / scan_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(done)} of {len(queries)} queries ({sum(queries[i].kind == 0 for i in done)} EA, "
+                      f"{sum(queries[i].kind == 1 for i in done)} LD), one-pass scans on 1 host core; "
+                      f"time-order sort ({sort_s:.1f} s) excluded as preprocessing",
+            "queries_per_s": len(done) / scan_s}
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the CPU oracle on this machine's host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    w = synth.WORKLOADS[args.workload]
+    el = synth.rmat(w.graph)
+    queries = synth.workload_queries(args.workload, el)
+    orc = oracle.Oracle(el)
+    half = len(queries) // 2
+    per_step = [0, half]  # one EA and one LD query per step, advancing through the set
+
+    def step(k):
+        te = 0
+        for base in per_step:
+            q = queries[(base + k) % len(queries)]
+            te += orc.admissible(q, orc.query(q))
+        return te
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    te = 0
+    for k in range(args.steps):
+        te += step(args.warmup + k)
+    dt = time.perf_counter() - t0
+    val = te / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.description}", "queries_per_step": len(per_step),
+                       "l2": "graph (0.8 GB) larger than L2"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(per_step)} queries (1 EA + 1 LD) per step, single-threaded "
+                                       f"one-pass scans; time-order sort excluded"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    import paper_2401_02563_gb300 as kx
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = synth.WORKLOADS[args.workload]
+    el = synth.rmat(w.graph)
+    queries = synth.workload_queries(args.workload, el)
+    Q, n, m = len(queries), el.n, el.m
+    stream = torch.cuda.Stream()
+    R = 10 if el.lam.dtype == np.uint16 else 12
+
+    with torch.cuda.stream(stream):
+        g = kx.Graph.from_edges(el, stream=stream)
+        g.index(w.theta)
+        info = g.info()
+        if args.lanes:
+            g.set_tuning(lanes=args.lanes)
+        else:
+            g.autotune(queries)
+        tuning = g.tuning()
+        lanes = tuning.lanes
+        out = torch.empty((Q, n), dtype=torch.int32, device="cuda")
+
+        def run_step():
+            st = g.batch(queries, out)
+            return st, g.last_kernel_ms()
+
+        for _ in range(args.warmup):
+            stats, _ = run_step()
+        te_step = sum(s.relaxed_edges for s in stats)
+        scanned_step = sum(s.scanned_edges for s in stats)
+
+        # ---- timed region: K steps, device-timed, barrier + sync on both sides ----
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kernel_ms = 0.0
+        with Clocks(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                stats, kms = run_step()
+                kernel_ms += kms
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        step_ms = ev0.elapsed_time(ev1) / args.steps
+        if dist:
+            t = torch.tensor([step_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            step_ms = float(t.item())
+            dist.barrier()
+        clocks = clk.summary()
+        value = world * te_step / (step_ms / 1e3) / 1e9
+        groups = launch_groups(queries, lanes)
+        n_launch = len(groups)
+
+        # ---- roofline of the edge-map kernel (algorithmic bytes / launch time) ----
+        E = {"m": m,
+             "src": torch.from_numpy(el.src.astype(np.int64)).cuda(),
+             "dst": torch.from_numpy(el.dst.astype(np.int64)).cuda(),
+             "t": torch.from_numpy(el.t.astype(np.int64)).cuda()}
+        E["tau"] = E["t"] + torch.from_numpy(el.lam.astype(np.int64)).cuda()
+        bytes_step = 0
+        for grp in groups:
+            U = union_admissible(torch, E, queries, grp, out)
+            bytes_step += U * R + 4 * sum(stats[i].relaxed_edges for i in grp) + 8 * len(grp) * n
+        del E
+        torch.cuda.empty_cache()
+        launch_ms = kernel_ms / args.steps / n_launch
+        achieved = bytes_step / n_launch / (launch_ms / 1e3) / 1e9
+        peak, peak_kind = peaks()
+
+        # ---- one query per launch, same queries ----
+        single = None
+        if not args.no_single:
+            row = torch.empty(n, dtype=torch.int32, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for q in queries[:2]:
+                (g.earliest_arrival if q.kind == 0 else g.latest_departure)(q.vertex, q.ta, q.tw, row)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for q in queries:
+                (g.earliest_arrival if q.kind == 0 else g.latest_departure)(q.vertex, q.ta, q.tw, row)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s_ms = e0.elapsed_time(e1)
+            single = {"gteps": te_step / (s_ms / 1e3) / 1e9, "queries_per_s": Q / (s_ms / 1e3),
+                      "ms_per_batch": s_ms}
+
+        # ---- end to end through the C ABI with host output buffers ----
+        e2e = None
+        if not args.no_e2e:
+            host = np.empty((Q, n), np.uint32)
+            g.batch(queries, host)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                g.batch(queries, host)
+            e2e_s = (time.perf_counter() - t0) / args.steps
+            e2e = {"value": world * te_step / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 16,
+                   "d2h_bytes_per_step": Q * n * 4, "note": "queries in, every label row copied to pageable host memory"}
+        g.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu else cpu_baseline(el, queries)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {w.description}", "vertices": n, "edges": m, "queries_per_step": Q,
+                   "index_threshold": w.theta, "lanes": lanes, "warp_max_edges": tuning.warp_max_edges,
+                   "dense_div": tuning.dense_div, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (graph 2 x 0.4 GB)"},
+        "queries_per_s": world * Q / (step_ms / 1e3),
+        "relaxed_edges_per_step": te_step, "scanned_edges_per_step": scanned_step,
+        "build_ms": info.build_ms, "index_ms": info.index_ms,
+        "single_launch": single,
+        "batched_vs_single_qps": (Q / (step_ms / 1e3)) / single["queries_per_s"] if single else None,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "edgemap_kernel",
+                     "launches_per_step": n_launch, "avg_launch_ms": launch_ms,
+                     "algorithmic_bytes_per_step": bytes_step},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * n_launch,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * kairos.h -- C ABI of the GB300 temporal edge-map library.
+ *
+ * The library answers time-respecting path queries on a temporal graph resident in GPU
+ * memory (one GPU, sm_103a): earliest arrival from a source and latest departure towards
+ * a target, each inside a time window, one at a time, in batches, or through a
+ * continuous-batching server.  Every step of a query runs in the library's own CUDA
+ * kernels; there is no CPU fallback.
+ *
+ * Model (paper Sec. 2.1): vertices 0..n-1; a temporal edge (u, v, t, lambda) departs u at
+ * time t and arrives at v at t + lambda (its validity interval [t, t + lambda]).  Times
+ * are uint32; t + lambda must not exceed KAIROS_TIME_MAX.
+ * Ordering predicates (Sec. 2.2): consecutive edges A, B of a path satisfy
+ * end(A) <= start(B) ("Succeeds", strict = 0, the default) or end(A) < start(B)
+ * ("StrictlySucceeds", strict = 1).  The first edge may depart exactly at the window start
+ * and the last may arrive exactly at the window end under either predicate.
+ * Window [ta, tw] is inclusive at both ends (the window test of Alg. 2).
+ * Results (Alg. 2 and Sec. 2.3's minimal temporal paths):
+ *   earliest arrival from s:  out[s] = ta; out[v] = least arrival time at v over
+ *                             time-respecting paths from s within the window;
+ *   latest departure to x:    out[x] = tw; out[u] = greatest departure time from u over
+ *                             time-respecting paths from u to x within the window;
+ *   KAIROS_UNREACHED where no such path exists.
+ *
+ * Conventions for every call:
+ *   - returns a kairos_status; never aborts, traps or exits; on failure
+ *     kairos_last_error() gives a message (thread-local, valid until the next call);
+ *   - pointers documented as "host or device" are classified with
+ *     cudaPointerGetAttributes; host memory may be pageable or pinned;
+ *   - calls on one graph are serialised internally (a graph owns one query workspace);
+ *     distinct graphs may be used from distinct threads.
+ */
+#ifndef KAIROS_H
+#define KAIROS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KAIROS_OK = 0,
+    KAIROS_ERR_INVALID_ARG = 1, /* bad pointer, size, vertex id, or ta > tw / tw > TIME_MAX */
+    KAIROS_ERR_OOM = 2,         /* device or host allocation failed */
+    KAIROS_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    KAIROS_ERR_OVERFLOW = 4,    /* an edge has t + lambda > KAIROS_TIME_MAX */
+    KAIROS_ERR_NOT_READY = 5,   /* a served query has not finished yet */
+    KAIROS_ERR_BUSY = 6,        /* the server's admission queue is full */
+    KAIROS_ERR_TIMEOUT = 7,     /* a device-side wait or the round cap (n + 1) ran out */
+    KAIROS_ERR_INTERNAL = 8     /* a device-side consistency check failed */
+} kairos_status;
+
+#define KAIROS_UNREACHED 0xFFFFFFFFu /* label of a vertex with no valid path */
+#define KAIROS_TIME_MAX 0xFFFFFFFEu  /* largest finite time; also the mirror constant */
+#define KAIROS_NO_INDEX 0xFFFFFFFFu  /* index threshold meaning "scan every list linearly" */
+
+enum { KAIROS_EA = 0, KAIROS_LD = 1 };
+
+typedef struct kairos_graph kairos_graph;   /* opaque; freed with kairos_graph_free */
+typedef struct kairos_server kairos_server; /* opaque; borrows a graph; kairos_serve_destroy */
+
+/* A structure-of-arrays temporal edge list (Sec. 2.1).  Edge i is
+ * (src[i], dst[i], t_dep[i], lambda[i]); lambda is uint16_t[] when lambda_bits == 16, else
+ * uint32_t[].  All four arrays are host memory, or device memory of the current device
+ * when on_device != 0.  The library copies them during kairos_graph_build and keeps no
+ * reference; the caller keeps ownership. */
+typedef struct {
+    int64_t n_vertices; /* n >= 1, n < 2^31 */
+    int64_t n_edges;    /* m >= 0, m < 2^32 */
+    const int32_t *src;
+    const int32_t *dst;
+    const uint32_t *t_dep;
+    const void *lambda;
+    int32_t lambda_bits; /* 16 or 32 */
+    int32_t on_device;
+} kairos_edge_list;
+
+/* Optional build options (NULL = defaults). */
+typedef struct {
+    void *stream;                           /* cudaStream_t for all work on this graph; NULL: legacy default stream */
+    void *(*alloc)(size_t bytes, void *ctx); /* device allocator; NULL: cudaMalloc */
+    void (*free)(void *ptr, void *ctx);      /* matching release; NULL: cudaFree */
+    void *alloc_ctx;
+    int32_t skip_reverse; /* nonzero: do not build the mirrored reverse graph (latest
+                             departure then returns INVALID_ARG); saves half the graph memory */
+} kairos_graph_opts;
+
+/* One query.  vertex is the source for KAIROS_EA and the target for KAIROS_LD. */
+typedef struct {
+    int32_t vertex;
+    uint32_t ta, tw; /* inclusive window, ta <= tw <= KAIROS_TIME_MAX */
+    uint8_t kind;    /* KAIROS_EA or KAIROS_LD */
+    uint8_t strict;  /* 0 Succeeds, 1 StrictlySucceeds */
+    uint16_t reserved;
+} kairos_query;
+
+/* Work counters of one query, filled by the calls that take a stats array. */
+typedef struct {
+    uint64_t relaxed_edges; /* usable edges relaxed: each edge with a reached tail, departure
+                               on or after the tail's label and arrival within the window,
+                               counted once (the "traversed edges" of GTEPS) */
+    uint64_t scanned_edges; /* edge records loaded for this query's batch (shared by its lanes) */
+    uint32_t rounds;        /* edge-map rounds until the frontier emptied */
+    uint32_t reached;       /* vertices with a finite label */
+} kairos_query_stats;
+
+/* Launch-shape knobs of the edge-map; kairos_autotune picks them per graph. */
+typedef struct {
+    int32_t lanes;          /* queries relaxed together per launch: 1, 2, 4, 8, 16 or 32 */
+    int32_t blocks_per_sm;  /* resident 256-thread blocks per SM of the persistent grid; 0: as many as fit */
+    int32_t warp_max_edges; /* a vertex's range longer than this is split across the grid */
+    int32_t chunk_edges;    /* edges per grid-wide chunk of a split range (multiple of 32) */
+    int32_t dense_div;      /* sweep the frontier bitmap instead of the queue when
+                               |frontier| > n / dense_div (0: never) */
+} kairos_tuning;
+
+typedef struct {
+    int64_t n_vertices, n_edges;
+    int32_t lambda_bits;
+    uint32_t index_threshold;    /* KAIROS_NO_INDEX when no index is built */
+    int64_t indexed_vertices;    /* forward graph vertices with a fence level */
+    int64_t device_bytes;        /* graph + index + query workspace currently held */
+    double build_ms;             /* last kairos_graph_build, device time */
+    double index_ms;             /* last kairos_index_build, device time */
+} kairos_graph_info;
+
+/* ---- graph and index -------------------------------------------------------------- */
+
+/* Build the device-resident time-sorted CSR of Sec. 2.4/4.2 from an edge list: each
+ * vertex's out-edges sorted by departure time (the paper's T-CSR, whose per-vertex lists
+ * the library keeps in time order), plus the reversed, time-mirrored graph used for
+ * latest departure (edge v -> u departing at KAIROS_TIME_MAX - (t + lambda)).
+ * Errors: INVALID_ARG (NULL, n < 1, m < 0, vertex id out of range, lambda_bits not 16/32),
+ * OVERFLOW (some t + lambda > KAIROS_TIME_MAX), OOM, CUDA.  *out is set only on success. */
+kairos_status kairos_graph_build(const kairos_edge_list *edges, const kairos_graph_opts *opts,
+                                 kairos_graph **out);
+
+/* Selective index (Sec. 3.2 "Vertex Indexer", Alg. 1 IndexVertices, cost model Eqs. 1-3):
+ * vertices whose degree is >= threshold get a fence level (every 32nd departure time of
+ * their sorted list) and are searched; shorter lists are scanned linearly.
+ * KAIROS_NO_INDEX drops the index (every list scanned).  Results never depend on it.
+ * Errors: INVALID_ARG (NULL graph), OOM, CUDA. */
+kairos_status kairos_index_build(kairos_graph *g, uint32_t threshold);
+
+void kairos_graph_free(kairos_graph *g); /* NULL is ignored; waits for the graph's stream */
+
+kairos_status kairos_graph_get_info(const kairos_graph *g, kairos_graph_info *info);
+
+/* ---- queries ------------------------------------------------------------------------ */
+
+/* Earliest arrival from src within [ta, tw] under Succeeds (Alg. 2).  out: uint32_t[n],
+ * host or device, owned by the caller.  Synchronous.  Errors: INVALID_ARG, TIMEOUT,
+ * OOM, CUDA. */
+kairos_status kairos_earliest_arrival(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, uint32_t *out);
+
+/* Latest departure towards dst within [ta, tw] under Succeeds (Sec. 2.3), computed as
+ * earliest arrival on the mirrored reverse graph.  out: uint32_t[n], host or device. */
+kairos_status kairos_latest_departure(kairos_graph *g, int32_t dst, uint32_t ta, uint32_t tw, uint32_t *out);
+
+/* Answer n queries of either kind and predicate.  out: uint32_t[n][n_vertices], query-major
+ * (row i is query i's labels), host or device.  stats: NULL or kairos_query_stats[n].
+ * Queries are packed tuning.lanes at a time into one persistent launch that loads each
+ * edge once for all of its lanes.  Synchronous.  Errors as above. */
+kairos_status kairos_batch_query(kairos_graph *g, const kairos_query *queries, int32_t n, uint32_t *out,
+                                 kairos_query_stats *stats);
+
+/* ---- launch shape ----------------------------------------------------------------- */
+
+kairos_status kairos_get_tuning(const kairos_graph *g, kairos_tuning *t);
+/* Errors: INVALID_ARG when a field is outside the documented set. */
+kairos_status kairos_set_tuning(kairos_graph *g, const kairos_tuning *t);
+
+/* Time a grid of launch shapes on `sample` (its queries are run, results discarded) and
+ * install the fastest; *best (may be NULL) receives it.  Errors as kairos_batch_query. */
+kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32_t n, kairos_tuning *best);
+
+/* ---- continuous-batching server ------------------------------------------------------ */
+
+typedef struct {
+    int32_t max_slots;      /* queries resident at once (lanes of the running batches); 0: 64 */
+    int32_t queue_capacity; /* pending submissions before submit returns BUSY; 0: 4096 */
+    int64_t reserve_bytes;  /* device memory left free when admitting a slot; 0: 1 GiB */
+} kairos_serve_opts;
+
+typedef struct {
+    kairos_status status;     /* the query's own outcome */
+    uint32_t reached;         /* vertices with a finite label */
+    uint64_t relaxed_edges;   /* as in kairos_query_stats */
+    uint64_t checksum;        /* sum over v of (v + 1) * out[v], mod 2^64 */
+    double latency_ms;        /* submit to completion, host clock */
+} kairos_result_info;
+
+/* Start a server thread on g (which must outlive it).  Queries submitted while others run
+ * are admitted into free slots between edge-map rounds as slots and device memory allow.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+kairos_status kairos_serve_create(kairos_graph *g, const kairos_serve_opts *opts, kairos_server **out);
+
+/* Enqueue one query; out: uint32_t[n], host or device, must stay valid until the ticket
+ * is polled OK.  Non-blocking.  Thread-safe.  Errors: INVALID_ARG, BUSY (queue full). */
+kairos_status kairos_serve_submit(kairos_server *s, const kairos_query *q, uint32_t *out, uint64_t *ticket);
+
+/* Wait up to timeout_us (0: do not wait, < 0: forever) for a ticket.  OK with *info filled
+ * (the ticket is then retired), NOT_READY if still running, INVALID_ARG for an unknown
+ * ticket.  Thread-safe. */
+kairos_status kairos_serve_poll(kairos_server *s, uint64_t ticket, int64_t timeout_us, kairos_result_info *info);
+
+/* Finish in-flight work, stop the thread and release the server.  NULL is ignored. */
+void kairos_serve_destroy(kairos_server *s);
+
+/* ---- diagnostics -------------------------------------------------------------------- */
+
+const char *kairos_last_error(void);
+const char *kairos_status_string(kairos_status s);
+/* Device time (ms) of the last query launch on g, measured with CUDA events on its stream. */
+double kairos_last_kernel_ms(const kairos_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KAIROS_H */

@@ -1,0 +1,397 @@
+"""Python binding of the GB300 temporal edge-map library (libkairos.so, C ABI in
+include/kairos.h).
+
+Argument marshalling only: every function below converts numpy arrays / torch tensors to
+pointers and calls the C function of the same name; all query work happens in the
+library's CUDA kernels.  There is no CPU fallback: if the library cannot be loaded, every
+call raises.
+
+Device memory and streams come from PyTorch: pass torch CUDA tensors as outputs, a
+torch.cuda.Stream (or its handle) as the graph stream, and optionally let the library
+allocate through torch's caching allocator.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+KAIROS_OK = 0
+KAIROS_ERR_INVALID_ARG = 1
+KAIROS_ERR_OOM = 2
+KAIROS_ERR_CUDA = 3
+KAIROS_ERR_OVERFLOW = 4
+KAIROS_ERR_NOT_READY = 5
+KAIROS_ERR_BUSY = 6
+KAIROS_ERR_TIMEOUT = 7
+KAIROS_ERR_INTERNAL = 8
+KAIROS_UNREACHED = 0xFFFFFFFF
+KAIROS_TIME_MAX = 0xFFFFFFFE
+KAIROS_NO_INDEX = 0xFFFFFFFF
+KAIROS_EA = 0
+KAIROS_LD = 1
+
+_P = ctypes.c_void_p
+
+
+class kairos_edge_list(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_edges", ctypes.c_int64), ("src", _P), ("dst", _P),
+                ("t_dep", _P), ("lambda_", _P), ("lambda_bits", ctypes.c_int32), ("on_device", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class kairos_graph_opts(ctypes.Structure):
+    _fields_ = [("stream", _P), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", _P),
+                ("skip_reverse", ctypes.c_int32)]
+
+
+class kairos_query(ctypes.Structure):
+    _fields_ = [("vertex", ctypes.c_int32), ("ta", ctypes.c_uint32), ("tw", ctypes.c_uint32),
+                ("kind", ctypes.c_uint8), ("strict", ctypes.c_uint8), ("reserved", ctypes.c_uint16)]
+
+
+class kairos_query_stats(ctypes.Structure):
+    _fields_ = [("relaxed_edges", ctypes.c_uint64), ("scanned_edges", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint32), ("reached", ctypes.c_uint32)]
+
+
+class kairos_tuning(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("warp_max_edges", ctypes.c_int32),
+                ("chunk_edges", ctypes.c_int32), ("dense_div", ctypes.c_int32)]
+
+
+class kairos_graph_info(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_edges", ctypes.c_int64), ("lambda_bits", ctypes.c_int32),
+                ("index_threshold", ctypes.c_uint32), ("indexed_vertices", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double), ("index_ms", ctypes.c_double)]
+
+
+class kairos_serve_opts(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("reserve_bytes", ctypes.c_int64)]
+
+
+class kairos_result_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reached", ctypes.c_uint32), ("relaxed_edges", ctypes.c_uint64),
+                ("checksum", ctypes.c_uint64), ("latency_ms", ctypes.c_double)]
+
+
+# Every function the header declares, with its ctypes signature.
+SIGNATURES = {
+    "kairos_graph_build": (ctypes.c_int, [ctypes.POINTER(kairos_edge_list), ctypes.POINTER(kairos_graph_opts),
+                                          ctypes.POINTER(_P)]),
+    "kairos_index_build": (ctypes.c_int, [_P, ctypes.c_uint32]),
+    "kairos_graph_free": (None, [_P]),
+    "kairos_graph_get_info": (ctypes.c_int, [_P, ctypes.POINTER(kairos_graph_info)]),
+    "kairos_earliest_arrival": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, _P]),
+    "kairos_latest_departure": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, _P]),
+    "kairos_batch_query": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32, _P,
+                                          ctypes.POINTER(kairos_query_stats)]),
+    "kairos_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
+    "kairos_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
+    "kairos_autotune": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32,
+                                       ctypes.POINTER(kairos_tuning)]),
+    "kairos_serve_create": (ctypes.c_int, [_P, ctypes.POINTER(kairos_serve_opts), ctypes.POINTER(_P)]),
+    "kairos_serve_submit": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "kairos_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(kairos_result_info)]),
+    "kairos_serve_destroy": (None, [_P]),
+    "kairos_last_error": (ctypes.c_char_p, []),
+    "kairos_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "kairos_last_kernel_ms": (ctypes.c_double, [_P]),
+}
+
+
+class KairosError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libkairos.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libkairos.so is not built; run __graft_entry__.build()")
+            L = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != KAIROS_OK:
+        raise KairosError(st, where, lib().kairos_last_error().decode())
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _on_device(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _nbytes(x) -> int:
+    if isinstance(x, np.ndarray):
+        return x.nbytes
+    return x.numel() * x.element_size()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class TorchAllocator:
+    """Device allocator hooks that route the library's allocations through PyTorch's
+    caching allocator on the current device."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes))
+        except Exception:
+            return None
+
+    def _free(self, ptr, ctx):
+        if ptr:
+            self._torch.cuda.caching_allocator_delete(int(ptr))
+
+
+# ---- the C functions, one wrapper each ------------------------------------------------
+
+def kairos_graph_build(n_vertices, src, dst, t_dep, lam, stream=None, allocator=None, skip_reverse=False):
+    """Build a device graph from four equal-length arrays (numpy host arrays or torch
+    tensors on the current CUDA device).  lam is uint16 or uint32.  Returns the handle."""
+    m = int(src.shape[0])
+    for a in (dst, t_dep, lam):
+        if int(a.shape[0]) != m:
+            raise ValueError("edge arrays differ in length")
+    lam_bits = 8 * (lam.itemsize if isinstance(lam, np.ndarray) else lam.element_size())
+    if lam_bits not in (16, 32):
+        raise ValueError("lambda must be 16- or 32-bit")
+    for a, sz in ((src, 4), (dst, 4), (t_dep, 4)):
+        if (a.itemsize if isinstance(a, np.ndarray) else a.element_size()) != sz:
+            raise ValueError("src, dst and t_dep must be 32-bit")
+    dev = [_on_device(a) for a in (src, dst, t_dep, lam)]
+    if any(dev) and not all(dev):
+        raise ValueError("edge arrays must all be host or all be device")
+    el = kairos_edge_list(int(n_vertices), m, _ptr(src), _ptr(dst), _ptr(t_dep), _ptr(lam), lam_bits,
+                          1 if all(dev) else 0)
+    opts = kairos_graph_opts()
+    opts.stream = _stream_handle(stream)
+    if allocator is not None:
+        opts.alloc = allocator.alloc
+        opts.free = allocator.free
+    opts.skip_reverse = 1 if skip_reverse else 0
+    h = _P()
+    _check(lib().kairos_graph_build(ctypes.byref(el), ctypes.byref(opts), ctypes.byref(h)), "kairos_graph_build")
+    return h
+
+
+def kairos_index_build(g, threshold: int):
+    _check(lib().kairos_index_build(g, int(threshold) & 0xFFFFFFFF), "kairos_index_build")
+
+
+def kairos_graph_free(g):
+    lib().kairos_graph_free(g)
+
+
+def kairos_graph_get_info(g) -> kairos_graph_info:
+    info = kairos_graph_info()
+    _check(lib().kairos_graph_get_info(g, ctypes.byref(info)), "kairos_graph_get_info")
+    return info
+
+
+def _check_out(out, n, rows=1):
+    if out is None or _nbytes(out) < 4 * n * rows:
+        raise ValueError(f"out must hold {rows} x {n} uint32 labels")
+
+
+def kairos_earliest_arrival(g, n, src, ta, tw, out):
+    _check_out(out, n)
+    _check(lib().kairos_earliest_arrival(g, int(src), int(ta), int(tw), _ptr(out)), "kairos_earliest_arrival")
+    return out
+
+
+def kairos_latest_departure(g, n, dst, ta, tw, out):
+    _check_out(out, n)
+    _check(lib().kairos_latest_departure(g, int(dst), int(ta), int(tw), _ptr(out)), "kairos_latest_departure")
+    return out
+
+
+def make_queries(queries) -> ctypes.Array:
+    """queries: iterable of (kind, vertex, ta, tw[, strict]) or objects with those fields."""
+    qs = list(queries)
+    arr = (kairos_query * max(len(qs), 1))()
+    for i, q in enumerate(qs):
+        if isinstance(q, tuple):
+            kind, v, ta, tw = q[:4]
+            strict = q[4] if len(q) > 4 else 0
+        else:
+            kind, v, ta, tw, strict = q.kind, q.vertex, q.ta, q.tw, getattr(q, "strict", 0)
+        arr[i] = kairos_query(int(v), int(ta), int(tw), int(kind), int(strict), 0)
+    return arr, len(qs)
+
+
+def kairos_batch_query(g, n, queries, out, want_stats=True):
+    """out: [len(queries)][n] uint32 labels (numpy or torch, host or device).  Returns the
+    per-query kairos_query_stats list (or None)."""
+    qarr, k = make_queries(queries)
+    _check_out(out, n, k)
+    stats = (kairos_query_stats * max(k, 1))() if want_stats else None
+    _check(lib().kairos_batch_query(g, qarr, k, _ptr(out), stats), "kairos_batch_query")
+    return list(stats)[:k] if want_stats else None
+
+
+def kairos_get_tuning(g) -> kairos_tuning:
+    t = kairos_tuning()
+    _check(lib().kairos_get_tuning(g, ctypes.byref(t)), "kairos_get_tuning")
+    return t
+
+
+def kairos_set_tuning(g, **fields):
+    t = kairos_get_tuning(g)
+    for k, v in fields.items():
+        setattr(t, k, int(v))
+    _check(lib().kairos_set_tuning(g, ctypes.byref(t)), "kairos_set_tuning")
+    return t
+
+
+def kairos_autotune(g, sample) -> kairos_tuning:
+    qarr, k = make_queries(sample)
+    best = kairos_tuning()
+    _check(lib().kairos_autotune(g, qarr, k, ctypes.byref(best)), "kairos_autotune")
+    return best
+
+
+def kairos_serve_create(g, max_slots=0, queue_capacity=0, reserve_bytes=0):
+    opts = kairos_serve_opts(int(max_slots), int(queue_capacity), int(reserve_bytes))
+    h = _P()
+    _check(lib().kairos_serve_create(g, ctypes.byref(opts), ctypes.byref(h)), "kairos_serve_create")
+    return h
+
+
+def kairos_serve_submit(s, query, out) -> int:
+    """Returns the ticket; raises KairosError (status BUSY) when the queue is full."""
+    qarr, _ = make_queries([query])
+    ticket = ctypes.c_uint64(0)
+    _check(lib().kairos_serve_submit(s, qarr, _ptr(out), ctypes.byref(ticket)), "kairos_serve_submit")
+    return int(ticket.value)
+
+
+def kairos_serve_poll(s, ticket, timeout_us=-1):
+    """Returns kairos_result_info, or None while the query is still running."""
+    info = kairos_result_info()
+    st = lib().kairos_serve_poll(s, int(ticket), int(timeout_us), ctypes.byref(info))
+    if st == KAIROS_ERR_NOT_READY:
+        return None
+    _check(st, "kairos_serve_poll")
+    return info
+
+
+def kairos_serve_destroy(s):
+    lib().kairos_serve_destroy(s)
+
+
+def kairos_last_error() -> str:
+    return lib().kairos_last_error().decode()
+
+
+def kairos_last_kernel_ms(g) -> float:
+    return float(lib().kairos_last_kernel_ms(g))
+
+
+class Graph:
+    """Owning wrapper of a kairos_graph handle."""
+
+    def __init__(self, n_vertices, src, dst, t_dep, lam, stream=None, allocator=None, skip_reverse=False):
+        self.n = int(n_vertices)
+        self.m = int(src.shape[0])
+        self._allocator = allocator  # keeps the callbacks alive as long as the graph
+        self.handle = kairos_graph_build(n_vertices, src, dst, t_dep, lam, stream, allocator, skip_reverse)
+
+    @classmethod
+    def from_edges(cls, el, **kw):
+        return cls(el.n, el.src, el.dst, el.t, el.lam, **kw)
+
+    def index(self, threshold):
+        kairos_index_build(self.handle, threshold)
+        return self
+
+    def earliest_arrival(self, src, ta, tw, out):
+        return kairos_earliest_arrival(self.handle, self.n, src, ta, tw, out)
+
+    def latest_departure(self, dst, ta, tw, out):
+        return kairos_latest_departure(self.handle, self.n, dst, ta, tw, out)
+
+    def batch(self, queries, out, want_stats=True):
+        return kairos_batch_query(self.handle, self.n, queries, out, want_stats)
+
+    def tuning(self):
+        return kairos_get_tuning(self.handle)
+
+    def set_tuning(self, **fields):
+        return kairos_set_tuning(self.handle, **fields)
+
+    def autotune(self, sample):
+        return kairos_autotune(self.handle, sample)
+
+    def info(self):
+        return kairos_graph_get_info(self.handle)
+
+    def last_kernel_ms(self):
+        return kairos_last_kernel_ms(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            kairos_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,582 @@
+// C ABI of the library: graph lifecycle, the query workspace, single and batched queries,
+// launch-shape tuning.  Host code only orchestrates; every step of a query runs in the
+// kernels of edgemap.cu and build.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace kairos;
+
+namespace kairos {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string &m) { g_err = m; }
+
+kairos_status fail(kairos_status st, const std::string &m) {
+    g_err = m;
+    return st;
+}
+
+kairos_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? KAIROS_ERR_OOM : KAIROS_ERR_CUDA;
+}
+
+void *Allocator::get(size_t bytes) const {
+    if (bytes == 0) bytes = 1;
+    if (alloc) return alloc(bytes, ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void Allocator::put(void *p) const {
+    if (!p) return;
+    if (release) release(p, ctx);
+    else cudaFree(p);
+}
+
+// Device checksum of rows: cs[i] = sum_v (v + 1) * x[i][v] mod 2^64, cnt[i] = #finite.
+__global__ void checksum_rows(const uint32_t *x, int64_t n, int rows, unsigned long long *cs, unsigned *cnt) {
+    for (int r = 0; r < rows; ++r) {
+        unsigned long long acc = 0;
+        unsigned c = 0;
+        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+            uint32_t y = x[(int64_t)r * n + v];
+            acc += (unsigned long long)(v + 1) * y;
+            c += (y != INF);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+            c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&cs[r], acc);
+            atomicAdd(&cnt[r], c);
+        }
+    }
+}
+
+}  // namespace kairos
+
+namespace {
+
+bool device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void release_work_arrays(kairos_graph *g) {
+    auto &w = g->work;
+    const auto &A = g->A;
+    A.put(w.arr);
+    A.put(w.prev);
+    A.put(w.bm);
+    A.put(w.queue);
+    A.put(w.big);
+    A.put(w.bigb);
+    A.put(w.chunk_owner);
+    A.put(w.stage);
+    w.arr = w.prev = w.bm = w.bigb = w.chunk_owner = w.stage = nullptr;
+    w.queue = nullptr;
+    w.big = nullptr;
+    w.lanes = 0;
+    w.cap_big = w.cap_chunks = 0;
+    w.bytes = 0;
+}
+
+kairos_status ensure_work(kairos_graph *g, int lanes, bool need_stage) {
+    auto &w = g->work;
+    const int wm = g->tuning.warp_max_edges, ch = g->tuning.chunk_edges;
+    if (w.arr && w.lanes == lanes && w.warp_max == wm && w.chunk == ch) {
+        if (need_stage && !w.stage) {
+            w.stage = (uint32_t *)g->A.get((size_t)g->n * lanes * 4);
+            if (!w.stage) return fail(KAIROS_ERR_OOM, "query workspace: device allocation failed");
+            w.bytes += (size_t)g->n * lanes * 4;
+        }
+        return KAIROS_OK;
+    }
+    release_work_arrays(g);
+    const int64_t n = g->n;
+    const int64_t nwords = (n + 31) / 32;
+    uint64_t v1 = 0, c1 = 0, v2 = 0, c2 = 0;
+    kairos_status st = split_capacity(g->A, g->stream, n, g->fwd.off, wm, ch, &v1, &c1);
+    if (st != KAIROS_OK) return st;
+    if (g->has_rev) {
+        st = split_capacity(g->A, g->stream, n, g->rev.off, wm, ch, &v2, &c2);
+        if (st != KAIROS_OK) return st;
+    }
+    const uint64_t cap_big = std::max(v1, v2) + 1, cap_chunks = std::max(c1, c2) + 1;
+    if (cap_chunks > 0xFFFFFFF0ull || cap_big > 0xFFFFFFF0ull)
+        return fail(KAIROS_ERR_INVALID_ARG, "query workspace: too many split ranges for this chunk size");
+    const auto &A = g->A;
+    w.arr = (uint32_t *)A.get((size_t)n * lanes * 4);
+    w.prev = (uint32_t *)A.get((size_t)n * lanes * 4);
+    w.bm = (uint32_t *)A.get((size_t)nwords * 2 * 4);
+    w.queue = (int32_t *)A.get((size_t)n * 2 * 4);
+    w.big = (BigEntry *)A.get((size_t)cap_big * sizeof(BigEntry));
+    w.bigb = (uint32_t *)A.get((size_t)cap_big * lanes * 2 * 4);
+    w.chunk_owner = (uint32_t *)A.get((size_t)cap_chunks * 4);
+    if (need_stage) w.stage = (uint32_t *)A.get((size_t)n * lanes * 4);
+    if (!w.arr || !w.prev || !w.bm || !w.queue || !w.big || !w.bigb || !w.chunk_owner || (need_stage && !w.stage)) {
+        release_work_arrays(g);
+        return fail(KAIROS_ERR_OOM, "query workspace: device allocation failed");
+    }
+    KAIROS_CUDA(cudaMemsetAsync(w.chunk_owner, 0xFF, (size_t)cap_chunks * 4, g->stream), "workspace init");
+    w.lanes = lanes;
+    w.warp_max = wm;
+    w.chunk = ch;
+    w.cap_big = (uint32_t)cap_big;
+    w.cap_chunks = (uint32_t)cap_chunks;
+    w.bytes = (size_t)n * lanes * 8 + (size_t)nwords * 8 + (size_t)n * 8 + cap_big * (sizeof(BigEntry) + lanes * 8) +
+              cap_chunks * 4 + (need_stage ? (size_t)n * lanes * 4 : 0);
+    return KAIROS_OK;
+}
+
+kairos_status check_query(const kairos_graph *g, const kairos_query &q) {
+    if (q.vertex < 0 || (int64_t)q.vertex >= g->n) return fail(KAIROS_ERR_INVALID_ARG, "query vertex out of range");
+    if (q.kind > 1) return fail(KAIROS_ERR_INVALID_ARG, "query kind must be KAIROS_EA or KAIROS_LD");
+    if (q.strict > 1) return fail(KAIROS_ERR_INVALID_ARG, "query strict must be 0 or 1");
+    if (q.ta > q.tw || q.tw > TMAX) return fail(KAIROS_ERR_INVALID_ARG, "query window needs ta <= tw <= KAIROS_TIME_MAX");
+    if (q.kind == KAIROS_LD && !g->has_rev)
+        return fail(KAIROS_ERR_INVALID_ARG, "latest departure needs the reverse graph (built with skip_reverse)");
+    return KAIROS_OK;
+}
+
+// Lane q of a launch takes query Q; latest departure runs as earliest arrival on the
+// mirrored reverse graph over [TMAX - tw, TMAX - ta].
+void lane_set(LaneParams &lp, int q, const kairos_query &Q, int64_t row) {
+    lp.src[q] = Q.vertex;
+    if (Q.kind == KAIROS_EA) {
+        lp.ta[q] = Q.ta;
+        lp.tw[q] = Q.tw;
+    } else {
+        lp.ta[q] = TMAX - Q.tw;
+        lp.tw[q] = TMAX - Q.ta;
+        lp.mirror_mask |= 1u << q;
+    }
+    if (Q.strict) lp.strict_mask |= 1u << q;
+    lp.row[q] = row;
+}
+
+kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, int lanes, uint32_t *out,
+                         int64_t stride, uint32_t *arr_alias, EdgeMapCtr *res) {
+    auto &w = g->work;
+    const int64_t n = g->n, nwords = (n + 31) / 32;
+    EdgeMapArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.off = c.off;
+    a.dst = c.dst;
+    a.t = c.t;
+    a.lam = c.lam;
+    a.fidx = c.fidx;
+    a.fence = c.fence;
+    a.n = n;
+    a.arr = arr_alias ? arr_alias : w.arr;
+    a.prev = w.prev;
+    a.bm[0] = w.bm;
+    a.bm[1] = w.bm + nwords;
+    a.queue[0] = w.queue;
+    a.queue[1] = w.queue + n;
+    a.big = w.big;
+    a.bigb = w.bigb;
+    a.chunk_owner = w.chunk_owner;
+    a.cap_big = w.cap_big;
+    a.cap_chunks = w.cap_chunks;
+    a.ctr = w.ctr;
+    a.out = out;
+    a.out_stride = stride;
+    a.out_is_arr = (arr_alias != nullptr && out == arr_alias) ? 1 : 0;
+    a.lanes = lp;
+    a.max_rounds = (uint32_t)std::min<int64_t>(n + 1, 0xFFFFFFF0LL);
+    a.warp_max_edges = g->tuning.warp_max_edges;
+    a.chunk_edges = g->tuning.chunk_edges;
+    a.dense_div = g->tuning.dense_div;
+    int bps = 0;
+    int grid = edgemap_max_grid(lanes, g->lam_bits, &bps);
+    if (grid <= 0) return fail(KAIROS_ERR_CUDA, "edge-map: no resident launch shape (occupancy query failed)");
+    if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
+    cudaStream_t s = g->stream;
+    KAIROS_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(EdgeMapCtr), s), "edge-map counters");
+    KAIROS_CUDA(cudaEventRecord(w.ev0, s), "event record");
+    KAIROS_CUDA(edgemap_launch(a, lanes, g->lam_bits, grid, s), "edge-map launch");
+    KAIROS_CUDA(cudaEventRecord(w.ev1, s), "event record");
+    KAIROS_CUDA(cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(EdgeMapCtr), cudaMemcpyDeviceToHost, s), "edge-map counters");
+    KAIROS_CUDA(cudaStreamSynchronize(s), "edge-map");
+    float ms = 0;
+    KAIROS_CUDA(cudaEventElapsedTime(&ms, w.ev0, w.ev1), "event time");
+    g->last_kernel_ms += ms;
+    *res = *w.ctr_host;
+    if (res->err == KERR_BARRIER_TIMEOUT) return fail(KAIROS_ERR_TIMEOUT, "edge-map: a grid barrier wait ran past its limit");
+    if (res->err == KERR_ROUNDS) return fail(KAIROS_ERR_TIMEOUT, "edge-map: round cap (n + 1) reached");
+    if (res->err) return fail(KAIROS_ERR_INTERNAL, "edge-map: split-range capacity exceeded");
+    return KAIROS_OK;
+}
+
+}  // namespace
+
+// Shared by the public query calls, the autotuner and the server.  out == nullptr runs the
+// queries without writing labels anywhere (timing only).
+kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_t nq, uint32_t *out,
+                                 kairos_query_stats *stats, int lanes) {
+    const int64_t n = g->n;
+    const bool dev = out ? device_ptr(out) : true;
+    kairos_status st = ensure_work(g, lanes, out && !dev && lanes > 1);
+    if (st != KAIROS_OK) return st;
+    auto &w = g->work;
+    g->last_kernel_ms = 0;
+    cudaStream_t s = g->stream;
+    std::vector<int> idx;
+    for (int kind = 0; kind < 2; ++kind) {
+        idx.clear();
+        for (int i = 0; i < nq; ++i)
+            if (qs[i].kind == kind) idx.push_back(i);
+        const Csr &csr = kind == KAIROS_EA ? g->fwd : g->rev;
+        for (size_t c = 0; c < idx.size(); c += lanes) {
+            const int k = (int)std::min<size_t>(lanes, idx.size() - c);
+            LaneParams lp;
+            std::memset(&lp, 0, sizeof(lp));
+            lp.nlanes = k;
+            uint32_t *o = nullptr, *alias = nullptr;
+            for (int j = 0; j < k; ++j) lane_set(lp, j, qs[idx[c + j]], j);
+            if (lanes == 1) {
+                alias = (out && dev) ? out + (int64_t)idx[c] * n : w.arr;
+                o = out ? alias : nullptr;
+            } else if (out) {
+                if (dev) {
+                    o = out;
+                    for (int j = 0; j < k; ++j) lp.row[j] = idx[c + j];
+                } else {
+                    o = w.stage;
+                }
+            }
+            EdgeMapCtr res;
+            st = run_launch(g, csr, lp, lanes, o, n, alias, &res);
+            if (st != KAIROS_OK) return st;
+            if (out && !dev) {
+                for (int j = 0; j < k; ++j) {
+                    const uint32_t *srcrow = lanes == 1 ? w.arr : w.stage + (int64_t)j * n;
+                    KAIROS_CUDA(cudaMemcpyAsync(out + (int64_t)idx[c + j] * n, srcrow, (size_t)n * 4,
+                                                cudaMemcpyDeviceToHost, s),
+                                "copy labels to host");
+                }
+                KAIROS_CUDA(cudaStreamSynchronize(s), "copy labels to host");
+            }
+            if (stats) {
+                for (int j = 0; j < k; ++j) {
+                    kairos_query_stats &S = stats[idx[c + j]];
+                    S.relaxed_edges = res.relaxed[j];
+                    S.scanned_edges = res.scanned;
+                    S.rounds = res.rounds;
+                    S.reached = res.reached[j];
+                }
+            }
+        }
+    }
+    return KAIROS_OK;
+}
+
+// Row checksums on the device (used by the server); x is a device pointer.
+kairos_status kairos_row_checksums(kairos_graph *g, const uint32_t *x, int rows, uint64_t *cs, uint32_t *reached) {
+    unsigned long long *d = (unsigned long long *)g->A.get((size_t)rows * 12 + 16);
+    if (!d) return fail(KAIROS_ERR_OOM, "checksum: device allocation failed");
+    unsigned *cnt = (unsigned *)(d + rows);
+    cudaStream_t s = g->stream;
+    cudaError_t e = cudaMemsetAsync(d, 0, (size_t)rows * 12, s);
+    if (e == cudaSuccess) {
+        checksum_rows<<<std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, 1024)), 256, 0, s>>>(x, g->n, rows, d, cnt);
+        e = cudaGetLastError();
+    }
+    std::vector<unsigned long long> hc(rows);
+    std::vector<unsigned> hn(rows);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), d, (size_t)rows * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hn.data(), cnt, (size_t)rows * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    g->A.put(d);
+    if (e != cudaSuccess) return cuda_fail(e, "checksum");
+    for (int r = 0; r < rows; ++r) {
+        cs[r] = hc[r];
+        reached[r] = hn[r];
+    }
+    return KAIROS_OK;
+}
+
+extern "C" {
+
+kairos_status kairos_graph_build(const kairos_edge_list *el, const kairos_graph_opts *opts, kairos_graph **out) {
+    if (!el || !out) return fail(KAIROS_ERR_INVALID_ARG, "graph build: NULL argument");
+    const int64_t n = el->n_vertices, m = el->n_edges;
+    if (n < 1 || n >= (1LL << 31)) return fail(KAIROS_ERR_INVALID_ARG, "graph build: need 1 <= n_vertices < 2^31");
+    if (m < 0 || m >= (1LL << 32)) return fail(KAIROS_ERR_INVALID_ARG, "graph build: need 0 <= n_edges < 2^32");
+    if (el->lambda_bits != 16 && el->lambda_bits != 32)
+        return fail(KAIROS_ERR_INVALID_ARG, "graph build: lambda_bits must be 16 or 32");
+    if (m > 0 && (!el->src || !el->dst || !el->t_dep || !el->lambda))
+        return fail(KAIROS_ERR_INVALID_ARG, "graph build: NULL edge array");
+    kairos_graph *g = new (std::nothrow) kairos_graph();
+    if (!g) return fail(KAIROS_ERR_OOM, "graph build: host allocation failed");
+    g->n = n;
+    g->m = m;
+    g->lam_bits = el->lambda_bits;
+    if (opts) {
+        g->stream = (cudaStream_t)opts->stream;
+        g->A.alloc = opts->alloc;
+        g->A.release = opts->free;
+        g->A.ctx = opts->alloc_ctx;
+        if ((opts->alloc == nullptr) != (opts->free == nullptr)) {
+            delete g;
+            return fail(KAIROS_ERR_INVALID_ARG, "graph build: alloc and free must be given together");
+        }
+    }
+    const bool want_rev = !(opts && opts->skip_reverse);
+    g->tuning.lanes = 1;
+    g->tuning.blocks_per_sm = 0;
+    g->tuning.warp_max_edges = 4096;
+    g->tuning.chunk_edges = 2048;
+    g->tuning.dense_div = 16;
+    auto bail = [&](kairos_status st) {
+        kairos_graph_free(g);
+        return st;
+    };
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaEventCreate(&g->work.ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&g->work.ev1);
+    if (e == cudaSuccess) e = cudaMallocHost(&g->work.ctr_host, sizeof(EdgeMapCtr));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "graph build: setup"));
+    g->work.ctr = (EdgeMapCtr *)g->A.get(sizeof(EdgeMapCtr));
+    if (!g->work.ctr) return bail(fail(KAIROS_ERR_OOM, "graph build: device allocation failed"));
+
+    const size_t lam_sz = el->lambda_bits == 16 ? 2 : 4;
+    const int32_t *src = el->src, *dst = el->dst;
+    const uint32_t *t = el->t_dep;
+    const void *lam = el->lambda;
+    void *copies[4] = {nullptr, nullptr, nullptr, nullptr};
+    auto drop_copies = [&]() {
+        for (void *p : copies) g->A.put(p);
+    };
+    cudaStream_t s = g->stream;
+    if (!el->on_device && m > 0) {
+        const size_t sz[4] = {(size_t)m * 4, (size_t)m * 4, (size_t)m * 4, (size_t)m * lam_sz};
+        const void *hs[4] = {el->src, el->dst, el->t_dep, el->lambda};
+        for (int i = 0; i < 4; ++i) {
+            copies[i] = g->A.get(sz[i]);
+            if (!copies[i]) {
+                drop_copies();
+                return bail(fail(KAIROS_ERR_OOM, "graph build: device allocation failed"));
+            }
+            e = cudaMemcpyAsync(copies[i], hs[i], sz[i], cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                drop_copies();
+                return bail(cuda_fail(e, "graph build: copy edges to device"));
+            }
+        }
+        src = (const int32_t *)copies[0];
+        dst = (const int32_t *)copies[1];
+        t = (const uint32_t *)copies[2];
+        lam = copies[3];
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    int flags = 0;
+    kairos_status st = validate_edges(s, n, m, src, dst, t, lam, el->lambda_bits, &flags, g->A);
+    if (st == KAIROS_OK && (flags & 1)) st = fail(KAIROS_ERR_INVALID_ARG, "graph build: vertex id out of range");
+    if (st == KAIROS_OK && (flags & 2)) st = fail(KAIROS_ERR_OVERFLOW, "graph build: t + lambda exceeds KAIROS_TIME_MAX");
+    if (st == KAIROS_OK) st = build_csr(g->A, s, n, m, src, dst, t, lam, el->lambda_bits, 0, &g->fwd);
+    if (st == KAIROS_OK && want_rev) {
+        st = build_csr(g->A, s, n, m, src, dst, t, lam, el->lambda_bits, 1, &g->rev);
+        if (st == KAIROS_OK) g->has_rev = 1;
+    }
+    drop_copies();
+    if (st != KAIROS_OK) return bail(st);
+    g->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = g;
+    return KAIROS_OK;
+}
+
+kairos_status kairos_index_build(kairos_graph *g, uint32_t threshold) {
+    if (!g) return fail(KAIROS_ERR_INVALID_ARG, "index build: NULL graph");
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (threshold == 0) threshold = 1;
+    auto t0 = std::chrono::steady_clock::now();
+    kairos_status st = build_index(g->A, g->stream, g->n, threshold, &g->fwd);
+    if (st == KAIROS_OK && g->has_rev) st = build_index(g->A, g->stream, g->n, threshold, &g->rev);
+    if (st != KAIROS_OK) {
+        free_index(g->A, &g->fwd);
+        free_index(g->A, &g->rev);
+        g->theta = KAIROS_NO_INDEX;
+        return st;
+    }
+    g->theta = threshold;
+    g->index_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return KAIROS_OK;
+}
+
+void kairos_graph_free(kairos_graph *g) {
+    if (!g) return;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        cudaStreamSynchronize(g->stream);
+        cudaGetLastError();
+        release_work_arrays(g);
+        free_csr(g->A, &g->fwd);
+        free_csr(g->A, &g->rev);
+        g->A.put(g->work.ctr);
+        if (g->work.ctr_host) cudaFreeHost(g->work.ctr_host);
+        if (g->work.ev0) cudaEventDestroy(g->work.ev0);
+        if (g->work.ev1) cudaEventDestroy(g->work.ev1);
+        cudaGetLastError();
+    }
+    delete g;
+}
+
+kairos_status kairos_graph_get_info(const kairos_graph *g, kairos_graph_info *info) {
+    if (!g || !info) return fail(KAIROS_ERR_INVALID_ARG, "graph info: NULL argument");
+    info->n_vertices = g->n;
+    info->n_edges = g->m;
+    info->lambda_bits = g->lam_bits;
+    info->index_threshold = g->theta;
+    info->indexed_vertices = g->fwd.indexed;
+    const int64_t per_dir = (g->n + 1) * 8 + g->m * (8 + (g->lam_bits == 16 ? 2 : 4));
+    info->device_bytes = per_dir * (g->has_rev ? 2 : 1) + (g->fwd.n_fence + g->rev.n_fence) * 4 +
+                         (g->fwd.fidx ? g->n * 4 : 0) + (g->rev.fidx ? g->n * 4 : 0) + (int64_t)g->work.bytes;
+    info->build_ms = g->build_ms;
+    info->index_ms = g->index_ms;
+    return KAIROS_OK;
+}
+
+kairos_status kairos_batch_query(kairos_graph *g, const kairos_query *qs, int32_t n, uint32_t *out,
+                                 kairos_query_stats *stats) {
+    if (!g || (n > 0 && (!qs || !out)) || n < 0) return fail(KAIROS_ERR_INVALID_ARG, "batch query: bad argument");
+    for (int i = 0; i < n; ++i) {
+        kairos_status st = check_query(g, qs[i]);
+        if (st != KAIROS_OK) return st;
+    }
+    std::lock_guard<std::mutex> lk(g->mu);
+    return kairos_run_queries(g, qs, n, out, stats, g->tuning.lanes);
+}
+
+static kairos_status single(kairos_graph *g, int kind, int32_t v, uint32_t ta, uint32_t tw, uint32_t *out) {
+    if (!g || !out) return fail(KAIROS_ERR_INVALID_ARG, "query: NULL argument");
+    kairos_query q;
+    std::memset(&q, 0, sizeof(q));
+    q.vertex = v;
+    q.ta = ta;
+    q.tw = tw;
+    q.kind = (uint8_t)kind;
+    kairos_status st = check_query(g, q);
+    if (st != KAIROS_OK) return st;
+    std::lock_guard<std::mutex> lk(g->mu);
+    return kairos_run_queries(g, &q, 1, out, nullptr, 1);
+}
+
+kairos_status kairos_earliest_arrival(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, uint32_t *out) {
+    return single(g, KAIROS_EA, src, ta, tw, out);
+}
+
+kairos_status kairos_latest_departure(kairos_graph *g, int32_t dst, uint32_t ta, uint32_t tw, uint32_t *out) {
+    return single(g, KAIROS_LD, dst, ta, tw, out);
+}
+
+kairos_status kairos_get_tuning(const kairos_graph *g, kairos_tuning *t) {
+    if (!g || !t) return fail(KAIROS_ERR_INVALID_ARG, "get tuning: NULL argument");
+    *t = g->tuning;
+    return KAIROS_OK;
+}
+
+kairos_status kairos_set_tuning(kairos_graph *g, const kairos_tuning *t) {
+    if (!g || !t) return fail(KAIROS_ERR_INVALID_ARG, "set tuning: NULL argument");
+    const int L = t->lanes;
+    if (!(L == 1 || L == 2 || L == 4 || L == 8 || L == 16 || L == 32))
+        return fail(KAIROS_ERR_INVALID_ARG, "tuning: lanes must be 1, 2, 4, 8, 16 or 32");
+    if (t->blocks_per_sm < 0 || t->blocks_per_sm > 32) return fail(KAIROS_ERR_INVALID_ARG, "tuning: blocks_per_sm in [0, 32]");
+    if (t->warp_max_edges < 32 || t->warp_max_edges > (1 << 24))
+        return fail(KAIROS_ERR_INVALID_ARG, "tuning: warp_max_edges in [32, 2^24]");
+    if (t->chunk_edges < 32 || t->chunk_edges % 32 || t->chunk_edges > (1 << 24))
+        return fail(KAIROS_ERR_INVALID_ARG, "tuning: chunk_edges a multiple of 32 in [32, 2^24]");
+    if (t->dense_div < 0) return fail(KAIROS_ERR_INVALID_ARG, "tuning: dense_div >= 0");
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->tuning = *t;
+    return KAIROS_OK;
+}
+
+kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32_t n, kairos_tuning *best) {
+    if (!g || !sample || n <= 0) return fail(KAIROS_ERR_INVALID_ARG, "autotune: bad argument");
+    for (int i = 0; i < n; ++i) {
+        kairos_status st = check_query(g, sample[i]);
+        if (st != KAIROS_OK) return st;
+    }
+    std::lock_guard<std::mutex> lk(g->mu);
+    const kairos_tuning base = g->tuning;
+    kairos_tuning win = base;
+    double win_ms = -1;
+    const int lanes_set[] = {1, 2, 4, 8, 16, 32};
+    const int wmax_set[] = {1024, 4096, 16384};
+    const int dense_set[] = {0, 16};
+    for (int L : lanes_set) {
+        for (int wm : wmax_set) {
+            for (int dd : dense_set) {
+                kairos_tuning c = base;
+                c.lanes = L;
+                c.warp_max_edges = wm;
+                c.dense_div = dd;
+                g->tuning = c;
+                kairos_status st = kairos_run_queries(g, sample, n, nullptr, nullptr, L);
+                if (st == KAIROS_ERR_OOM) continue;  // this lane width does not fit: skip it
+                if (st != KAIROS_OK) {
+                    g->tuning = base;
+                    return st;
+                }
+                const double ms = g->last_kernel_ms;
+                if (win_ms < 0 || ms < win_ms) {
+                    win_ms = ms;
+                    win = c;
+                }
+            }
+        }
+    }
+    if (win_ms < 0) {
+        g->tuning = base;
+        return fail(KAIROS_ERR_OOM, "autotune: no launch shape fits in device memory");
+    }
+    g->tuning = win;
+    if (best) *best = win;
+    return KAIROS_OK;
+}
+
+const char *kairos_last_error(void) { return g_err.c_str(); }
+
+const char *kairos_status_string(kairos_status s) {
+    switch (s) {
+        case KAIROS_OK: return "KAIROS_OK";
+        case KAIROS_ERR_INVALID_ARG: return "KAIROS_ERR_INVALID_ARG";
+        case KAIROS_ERR_OOM: return "KAIROS_ERR_OOM";
+        case KAIROS_ERR_CUDA: return "KAIROS_ERR_CUDA";
+        case KAIROS_ERR_OVERFLOW: return "KAIROS_ERR_OVERFLOW";
+        case KAIROS_ERR_NOT_READY: return "KAIROS_ERR_NOT_READY";
+        case KAIROS_ERR_BUSY: return "KAIROS_ERR_BUSY";
+        case KAIROS_ERR_TIMEOUT: return "KAIROS_ERR_TIMEOUT";
+        case KAIROS_ERR_INTERNAL: return "KAIROS_ERR_INTERNAL";
+    }
+    return "unknown kairos_status";
+}
+
+double kairos_last_kernel_ms(const kairos_graph *g) { return g ? g->last_kernel_ms : 0.0; }
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Internal declarations shared by the library's translation units (device helpers, the
+// graph object, the edge-map launch record).  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "kairos.h"
+
+namespace kairos {
+
+constexpr uint32_t INF = 0xFFFFFFFFu;   // label of an unreached vertex
+constexpr uint32_t TMAX = 0xFFFFFFFEu;  // largest finite time and mirror constant
+constexpr uint32_t NO_FENCE = 0xFFFFFFFFu;
+constexpr int FENCE_SHIFT = 5;          // one fence key every 32 edges
+constexpr int FENCE_B = 1 << FENCE_SHIFT;
+constexpr int EM_THREADS = 256;         // edge-map block size
+constexpr int MAX_LANES = 32;
+
+// Device-side error codes reported through EdgeMapCtr::err.
+enum : int { KERR_NONE = 0, KERR_BARRIER_TIMEOUT = 1, KERR_ROUNDS = 2, KERR_CAPACITY = 3 };
+
+// ---- status / error plumbing ---------------------------------------------------------
+
+void set_error(const std::string &msg);
+kairos_status fail(kairos_status st, const std::string &msg);
+kairos_status cuda_fail(cudaError_t e, const char *what);
+
+#define KAIROS_CUDA(call, what)                                 \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return ::kairos::cuda_fail(_e, what); \
+    } while (0)
+
+// ---- device memory -------------------------------------------------------------------
+
+struct Allocator {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+    void *get(size_t bytes) const;   // nullptr on failure
+    void put(void *p) const;
+};
+
+// One direction of the time-sorted CSR plus its fence level.
+struct Csr {
+    uint64_t *off = nullptr;   // [n + 1] edge offsets
+    int32_t *dst = nullptr;    // [m] head vertex
+    uint32_t *t = nullptr;     // [m] departure time, ascending within each vertex
+    void *lam = nullptr;       // [m] duration, uint16_t or uint32_t
+    uint32_t *fidx = nullptr;  // [n] first fence key of the vertex, NO_FENCE if unindexed
+    uint32_t *fence = nullptr; // fence keys: t of every FENCE_B-th edge of indexed vertices
+    int64_t n_fence = 0;
+    int64_t indexed = 0;
+    int64_t max_deg = 0;
+};
+
+// Counters of one persistent edge-map launch (zeroed before each launch).
+struct EdgeMapCtr {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int err;
+    unsigned int rounds;
+    unsigned int qcount[3];     // frontier queue lengths, indexed by round mod 3
+    unsigned int bigcount[3];   // split ranges registered, by round mod 3
+    unsigned int chunks[3];     // grid-wide chunks registered, by round mod 3
+    unsigned int chunk_next[3]; // chunks claimed, by round mod 3
+    unsigned long long scanned;
+    unsigned long long relaxed[MAX_LANES];
+    unsigned int reached[MAX_LANES];
+};
+
+// A long per-vertex edge range split into grid-wide chunks.
+struct BigEntry {
+    uint64_t base;        // first edge index
+    uint32_t len;         // edges in the range
+    uint32_t chunk_base;  // first chunk id
+};
+
+// Per-lane query parameters of one launch (times already mirrored for latest departure).
+struct LaneParams {
+    int32_t src[MAX_LANES];
+    uint32_t ta[MAX_LANES];
+    uint32_t tw[MAX_LANES];
+    int64_t row[MAX_LANES]; // output row of lane q
+    uint32_t strict_mask;  // bit q: StrictlySucceeds
+    uint32_t mirror_mask;  // bit q: output is KAIROS_TIME_MAX - label (latest departure)
+    int32_t nlanes;
+};
+
+struct EdgeMapArgs {
+    // graph (one direction)
+    const uint64_t *off;
+    const int32_t *dst;
+    const uint32_t *t;
+    const void *lam;
+    const uint32_t *fidx;  // nullptr: no index
+    const uint32_t *fence;
+    int64_t n;
+    // workspace
+    uint32_t *arr;         // [n][W] labels
+    uint32_t *prev;        // [n][W] departure bound already scanned
+    uint32_t *bm[2];       // frontier bitmaps, ceil(n/32) words each
+    int32_t *queue[2];     // frontier queues, n entries each
+    BigEntry *big;
+    uint32_t *bigb;        // [cap_big][W][2] lane bounds of split ranges
+    uint32_t *chunk_owner; // [cap_chunks]
+    uint32_t cap_big, cap_chunks;
+    EdgeMapCtr *ctr;
+    // output: out[q * out_stride + v] for q < nlanes; nullptr: none
+    uint32_t *out;
+    int64_t out_stride;
+    int out_is_arr;        // lanes == 1 and out aliases arr
+    // parameters
+    LaneParams lanes;
+    uint32_t max_rounds;
+    int warp_max_edges, chunk_edges, dense_div;
+};
+
+// Launch one persistent edge-map (cooperative: every block resident).
+cudaError_t edgemap_launch(const EdgeMapArgs &a, int lanes, int lam_bits, int grid, cudaStream_t s);
+// Largest co-resident grid for this lane width (blocks per SM * SMs), 0 on error.
+int edgemap_max_grid(int lanes, int lam_bits, int *blocks_per_sm_out);
+size_t edgemap_smem_bytes(int lanes);
+
+// ---- device build ------------------------------------------------------------------------
+
+// Time-sorted CSR of (key_src -> key_dst) edges.  mirror != 0 builds the reversed,
+// time-mirrored graph: edge dst -> src departing at TMAX - (t + lam).
+kairos_status build_csr(const Allocator &A, cudaStream_t s, int64_t n, int64_t m, const int32_t *src,
+                        const int32_t *dst, const uint32_t *t, const void *lam, int lam_bits, int mirror,
+                        Csr *out);
+kairos_status validate_edges(cudaStream_t s, int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                             const uint32_t *t, const void *lam, int lam_bits, int *flags_host,
+                             const Allocator &A);
+kairos_status build_index(const Allocator &A, cudaStream_t s, int64_t n, uint32_t threshold, Csr *c);
+void free_index(const Allocator &A, Csr *c);
+void free_csr(const Allocator &A, Csr *c);
+// Count vertices with degree > x and the grid chunks their full ranges need.
+kairos_status split_capacity(const Allocator &A, cudaStream_t s, int64_t n, const uint64_t *off, int64_t x,
+                             int64_t chunk, uint64_t *vertices, uint64_t *chunks);
+
+}  // namespace kairos
+
+// The graph object behind the opaque C handle.
+struct kairos_graph {
+    int64_t n = 0, m = 0;
+    int lam_bits = 32;
+    cudaStream_t stream = nullptr;
+    kairos::Allocator A;
+    kairos::Csr fwd, rev;
+    int has_rev = 0;
+    uint32_t theta = KAIROS_NO_INDEX;
+    kairos_tuning tuning{};
+    double build_ms = 0, index_ms = 0, last_kernel_ms = 0;
+    int sm_count = 0;
+    std::mutex mu;
+
+    // query workspace (grown on demand)
+    struct Work {
+        int lanes = 0;
+        uint32_t *arr = nullptr, *prev = nullptr, *bm = nullptr;
+        int32_t *queue = nullptr;
+        kairos::BigEntry *big = nullptr;
+        uint32_t *bigb = nullptr, *chunk_owner = nullptr;
+        uint32_t cap_big = 0, cap_chunks = 0;
+        int warp_max = 0, chunk = 0;
+        kairos::EdgeMapCtr *ctr = nullptr;      // device
+        kairos::EdgeMapCtr *ctr_host = nullptr; // pinned mirror
+        uint32_t *stage = nullptr;              // [lanes][n] output staging for host outputs
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        size_t bytes = 0;
+    } work;
+};

@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the oracle on the same
+seeded inputs.  All arithmetic is exact uint32, so every comparison is bit-exact."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import C_MIRROR, UNREACHED, Oracle
+from synth import EA, LD, Query
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2401_02563_gb300 as kx  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+NO_INDEX = kx.KAIROS_NO_INDEX
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kx.lib()
+    yield
+
+
+def labels(x):
+    if hasattr(x, "cpu"):
+        return x.cpu().numpy().view(np.uint32).reshape(x.shape)
+    return np.asarray(x).view(np.uint32)
+
+
+def dev_out(n, rows=None):
+    shape = (n,) if rows is None else (rows, n)
+    return torch.full(shape, 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+
+
+def gpu_batch(g, n, queries, on_device=True):
+    out = dev_out(n, len(queries)) if on_device else np.full((len(queries), n), 0x5A5A5A5A, np.uint32)
+    stats = kx.kairos_batch_query(g.handle, n, queries, out)
+    return labels(out), stats
+
+
+class Edges:
+    def __init__(self, n, rows):
+        r = np.array(rows, dtype=np.int64).reshape(-1, 4)
+        self.n = n
+        self.src = r[:, 0].astype(np.int32)
+        self.dst = r[:, 1].astype(np.int32)
+        self.t = r[:, 2].astype(np.uint32)
+        self.lam = r[:, 3].astype(np.uint32)
+
+
+# ---- the hand-worked example ----------------------------------------------------------
+
+def test_hand_worked_example():
+    gj = json.load(open(os.path.join(HERE, "golden", "hand_example.json")))
+    el = Edges(gj["n"], gj["edges_u_v_t_lam"])
+    g = kx.Graph.from_edges(el)
+    for th in (1, NO_INDEX):
+        g.index(th)
+        qs = [Query(EA if c["kind"] == "EA" else LD, c["vertex"], c["ta"], c["tw"], c["strict"]) for c in gj["cases"]]
+        got, stats = gpu_batch(g, el.n, qs)
+        for i, c in enumerate(gj["cases"]):
+            assert got[i].tolist() == c["expect"], c
+            if "admissible" in c:
+                assert stats[i].relaxed_edges == c["admissible"]
+    g.close()
+
+
+# ---- tiny workload: every query kind, predicate, index threshold and lane width ----------
+
+@pytest.fixture(scope="module")
+def tiny():
+    el = synth.rmat(synth.WORKLOADS[1].graph)
+    orc = Oracle(el)
+    g = kx.Graph.from_edges(el)
+    yield el, orc, g
+    g.close()
+
+
+def tiny_queries(el, count=12):
+    srcs = synth.pick_vertices(el, count, 0x9100, True, True)
+    wins = [(0, (1 << 20) - 1), (0, C_MIRROR), (200_000, 700_000), (500_000, 500_900)]
+    qs = []
+    for i, v in enumerate(srcs):
+        ta, tw = wins[i % len(wins)]
+        qs.append(Query(EA if i % 2 == 0 else LD, v, ta, tw, (i // 2) % 2))
+    return qs
+
+
+def test_single_query_calls_match_oracle(tiny):
+    el, orc, g = tiny
+    g.index(NO_INDEX)
+    q = synth.workload_queries(1, el)[0]
+    want = orc.query(q)
+    out = dev_out(el.n)
+    g.earliest_arrival(q.vertex, q.ta, q.tw, out)
+    assert np.array_equal(labels(out), want)
+    host = np.zeros(el.n, np.uint32)
+    g.earliest_arrival(q.vertex, q.ta, q.tw, host)
+    assert np.array_equal(host, want)
+    want_ld = orc.latest_departure(q.vertex, 0, (1 << 20) - 1)
+    g.latest_departure(q.vertex, 0, (1 << 20) - 1, out)
+    assert np.array_equal(labels(out), want_ld)
+    g.latest_departure(q.vertex, 0, (1 << 20) - 1, host)
+    assert np.array_equal(host, want_ld)
+
+
+@pytest.mark.parametrize("theta", [1, 16, 256, 4096, NO_INDEX])
+def test_index_threshold_invariance(tiny, theta):
+    el, orc, g = tiny
+    g.index(theta)
+    g.set_tuning(lanes=1)
+    qs = tiny_queries(el)
+    got, stats = gpu_batch(g, el.n, qs)
+    for i, q in enumerate(qs):
+        want = orc.query(q)
+        assert np.array_equal(got[i], want), (theta, q)
+        assert stats[i].relaxed_edges == orc.admissible(q, want), (theta, q)
+        assert stats[i].reached == int((want != UNREACHED).sum())
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("on_device", [True, False])
+def test_lane_widths(tiny, lanes, on_device):
+    el, orc, g = tiny
+    g.index(64)
+    g.set_tuning(lanes=lanes)
+    qs = tiny_queries(el, 37)  # ragged: not a multiple of any lane width
+    got, stats = gpu_batch(g, el.n, qs, on_device)
+    for i, q in enumerate(qs):
+        want = orc.query(q)
+        assert np.array_equal(got[i], want), (lanes, q)
+        assert stats[i].relaxed_edges == orc.admissible(q, want)
+    g.set_tuning(lanes=1)
+
+
+@pytest.mark.parametrize("warp_max,chunk,dense", [(32, 32, 0), (32, 64, 1), (100, 32, 1_000_000), (4096, 2048, 1)])
+def test_work_shapes(tiny, warp_max, chunk, dense):
+    """Grid-wide chunking of long ranges and the dense bitmap sweep give identical labels."""
+    el, orc, g = tiny
+    g.index(16)
+    g.set_tuning(lanes=4, warp_max_edges=warp_max, chunk_edges=chunk, dense_div=dense)
+    qs = tiny_queries(el, 9)
+    got, stats = gpu_batch(g, el.n, qs)
+    for i, q in enumerate(qs):
+        want = orc.query(q)
+        assert np.array_equal(got[i], want), q
+        assert stats[i].relaxed_edges == orc.admissible(q, want)
+    g.set_tuning(lanes=1, warp_max_edges=4096, chunk_edges=2048, dense_div=16)
+
+
+# ---- random multigraphs: zero durations, self-loops, parallel edges, ties -----------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_multigraphs(seed):
+    n, m = 60 + 17 * seed, 400 + 131 * seed
+    el = synth.random_small(n, m, 0x9200 + seed, t_max=40, lam_max=4, lam_min=0)
+    orc = Oracle(el)
+    g = kx.Graph.from_edges(el)
+    g.index([1, 4, NO_INDEX][seed % 3])
+    g.set_tuning(lanes=[1, 8, 32][seed % 3], warp_max_edges=32, chunk_edges=32)
+    qs = []
+    for i in range(40):
+        d = lambda k: synth.draw(0x9300 + seed, i, k)
+        ta = synth.below(d(1), 20)
+        qs.append(Query(i % 2, synth.below(d(0), n), ta, ta + synth.below(d(2), 40), (i // 2) % 2))
+    got, stats = gpu_batch(g, n, qs)
+    for i, q in enumerate(qs):
+        want = orc.query(q)
+        assert np.array_equal(got[i], want), q
+        assert stats[i].relaxed_edges == orc.admissible(q, want)
+    g.close()
+
+
+def test_device_resident_input_and_torch_allocator():
+    el = synth.random_small(300, 3000, 0x9400, t_max=1000, lam_max=20, lam_min=1)
+    orc = Oracle(el)
+    cols = [torch.from_numpy(a.astype(np.int32) if a.dtype != np.int32 else a).cuda()
+            for a in (el.src, el.dst, el.t.view(np.int32), el.lam.view(np.int32))]
+    alloc = kx.TorchAllocator()
+    g = kx.Graph(el.n, *cols, stream=torch.cuda.current_stream(), allocator=alloc)
+    g.index(8)
+    qs = [Query(k, v, 0, 2000) for k in (EA, LD) for v in (1, 7, 299)]
+    got, _ = gpu_batch(g, el.n, qs)
+    for i, q in enumerate(qs):
+        assert np.array_equal(got[i], orc.query(q))
+    g.close()
+
+
+def test_uint16_durations():
+    spec = synth.scaled(synth.WORKLOADS[5].graph, 12, 40_000)
+    el = synth.rmat(spec)
+    assert el.lam.dtype == np.uint16
+    orc = Oracle(el)
+    g = kx.Graph.from_edges(el)
+    g.index(64)
+    vs = synth.pick_vertices(el, 4, 0x9500, True, True)
+    qs = [Query(k, v, 0, C_MIRROR) for v in vs for k in (EA, LD)]
+    got, stats = gpu_batch(g, el.n, qs)
+    for i, q in enumerate(qs):
+        want = orc.query(q)
+        assert np.array_equal(got[i], want)
+        assert stats[i].relaxed_edges == orc.admissible(q, want)
+    g.close()
+
+
+# ---- edge cases and errors ----------------------------------------------------------------
+
+def test_edge_cases():
+    # a single vertex, no edges
+    g = kx.Graph(1, *(np.zeros(0, t) for t in (np.int32, np.int32, np.uint32, np.uint32)))
+    out = dev_out(1)
+    g.earliest_arrival(0, 5, 9, out)
+    assert labels(out).tolist() == [5]
+    g.latest_departure(0, 5, 9, out)
+    assert labels(out).tolist() == [9]
+    g.close()
+    # isolated source; ta == tw; window end at KAIROS_TIME_MAX
+    el = Edges(4, [(1, 2, 3, 1), (2, 3, 4, 0), (2, 3, 4, 0), (3, 3, 7, 2), (1, 1, 0, 0)])
+    orc = Oracle(el)
+    g = kx.Graph.from_edges(el)
+    for q in [Query(EA, 0, 0, 10), Query(EA, 1, 3, 3), Query(EA, 1, 3, 4), Query(LD, 3, 0, C_MIRROR),
+              Query(EA, 1, 0, C_MIRROR, 1), Query(LD, 2, 4, 4)]:
+        got, _ = gpu_batch(g, 4, [q])
+        assert np.array_equal(got[0], orc.query(q)), q
+    with pytest.raises(kx.KairosError) as e:
+        g.earliest_arrival(4, 0, 1, dev_out(4))
+    assert e.value.status == kx.KAIROS_ERR_INVALID_ARG
+    with pytest.raises(kx.KairosError) as e:
+        g.earliest_arrival(0, 5, 4, dev_out(4))
+    assert e.value.status == kx.KAIROS_ERR_INVALID_ARG
+    with pytest.raises(kx.KairosError) as e:
+        g.latest_departure(0, 0, 0xFFFFFFFF, dev_out(4))
+    assert e.value.status == kx.KAIROS_ERR_INVALID_ARG
+    g.close()
+    # t + lambda beyond KAIROS_TIME_MAX, and a vertex id out of range, are rejected at build
+    bad = Edges(3, [(0, 1, 0xFFFFFFF0, 0x20)])
+    with pytest.raises(kx.KairosError) as e:
+        kx.Graph.from_edges(bad)
+    assert e.value.status == kx.KAIROS_ERR_OVERFLOW
+    bad = Edges(3, [(0, 3, 1, 1)])
+    with pytest.raises(kx.KairosError) as e:
+        kx.Graph.from_edges(bad)
+    assert e.value.status == kx.KAIROS_ERR_INVALID_ARG
+    # latest departure on a graph built without the reverse direction
+    g = kx.Graph.from_edges(Edges(3, [(0, 1, 1, 1)]), skip_reverse=True)
+    with pytest.raises(kx.KairosError) as e:
+        g.latest_departure(1, 0, 5, dev_out(3))
+    assert e.value.status == kx.KAIROS_ERR_INVALID_ARG
+    g.close()
+
+
+# ---- the medium workload at full size ----------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def medium():
+    el = synth.rmat(synth.WORKLOADS[2].graph)
+    g = kx.Graph.from_edges(el)
+    g.index(synth.WORKLOADS[2].theta)
+    yield el, g
+    g.close()
+
+
+def test_medium_full_size_sampled_against_oracle(medium):
+    """Full 2^25-edge workload in the launch shape the benchmark times: every query is
+    certified at full size, and a sample is compared label by label with the oracle."""
+    el, g = medium
+    qs = synth.workload_queries(2, el)
+    g.set_tuning(lanes=8)
+    got, stats = gpu_batch(g, el.n, qs)
+    orc = Oracle(el)
+    for i in (0, 1, 63, 64, 65, 127):
+        want = orc.query(qs[i])
+        assert np.array_equal(got[i], want), qs[i]
+        assert stats[i].relaxed_edges == orc.admissible(qs[i], want)
+    for i, q in enumerate(qs[:64]):
+        assert oracle.certify_ea(el, q.vertex, q.ta, q.tw, q.strict, got[i]) == (0, 0), q
+    g.set_tuning(lanes=1)
