@@ -237,14 +237,14 @@ def main():
         lanes = tuning.lanes
         out = torch.empty((Q, n), dtype=torch.int32, device="cuda")
 
-        def run_step():
-            st = g.batch(queries, out)
+        def run_step(with_stats=False):
+            st = g.batch(queries, out, want_stats=with_stats)
             return st, g.last_kernel_ms()
 
+        # exact per-query counts (TE, rounds, reached) from one untimed pass with statistics
+        stats, _ = run_step(with_stats=True)
         for _ in range(args.warmup):
-            stats, _ = run_step()
-        te_step = sum(s.relaxed_edges for s in stats)
-        scanned_step = sum(s.scanned_edges for s in stats)
+            run_step()
 
         # ---- timed region: K steps, device-timed, barrier + sync on both sides ----
         if dist:
@@ -255,11 +255,13 @@ def main():
         with Clocks(local) as clk:
             ev0.record(stream)
             for _ in range(args.steps):
-                stats, kms = run_step()
+                _, kms = run_step()
                 kernel_ms += kms
             ev1.record(stream)
             torch.cuda.synchronize()
         step_ms = ev0.elapsed_time(ev1) / args.steps
+        te_step = sum(s.relaxed_edges for s in stats)  # identical every step: exact integer counts
+        scanned_step = sum(s.scanned_edges for s in stats) // lanes  # one count per launch
         if dist:
             t = torch.tensor([step_ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)

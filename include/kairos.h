@@ -213,8 +213,17 @@ void kairos_serve_destroy(kairos_server *s);
 
 const char *kairos_last_error(void);
 const char *kairos_status_string(kairos_status s);
-/* Device time (ms) of the last query launch on g, measured with CUDA events on its stream. */
+/* Device time (ms) of the last query call's edge-map launches on g (sum), measured with
+ * CUDA events on the graph's stream. */
 double kairos_last_kernel_ms(const kairos_graph *g);
+
+/* Round profile of the last edge-map launch on g: per round (up to max_rounds, at most
+ * 256) the frontier size, the number of grid-wide chunks its long ranges were cut into, and
+ * the round's device time in ms (from the GPU's global timer).  Any output may be NULL.
+ * Returns the number of rounds written.  Diagnostic only; not synchronised with other
+ * threads using g. */
+int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uint32_t *frontier, uint32_t *chunks,
+                                  double *ms);
 
 #ifdef __cplusplus
 }

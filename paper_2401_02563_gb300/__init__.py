@@ -108,6 +108,7 @@ SIGNATURES = {
     "kairos_last_error": (ctypes.c_char_p, []),
     "kairos_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "kairos_last_kernel_ms": (ctypes.c_double, [_P]),
+    "kairos_last_round_profile": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P]),
 }
 
 
@@ -342,6 +343,15 @@ def kairos_last_error() -> str:
 
 def kairos_last_kernel_ms(g) -> float:
     return float(lib().kairos_last_kernel_ms(g))
+
+
+def kairos_last_round_profile(g, max_rounds=256):
+    """(frontier sizes, chunk counts, ms) per round of the last edge-map launch."""
+    f = np.zeros(max_rounds, np.uint32)
+    c = np.zeros(max_rounds, np.uint32)
+    ms = np.zeros(max_rounds, np.float64)
+    r = lib().kairos_last_round_profile(g, max_rounds, f.ctypes.data, c.ctypes.data, ms.ctypes.data)
+    return f[:r], c[:r], ms[:r]
 
 
 class Graph:

@@ -177,7 +177,7 @@ void lane_set(LaneParams &lp, int q, const kairos_query &Q, int64_t row) {
 }
 
 kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, int lanes, uint32_t *out,
-                         int64_t stride, uint32_t *arr_alias, EdgeMapCtr *res) {
+                         int64_t stride, uint32_t *arr_alias, int count_relaxed, EdgeMapCtr *res) {
     auto &w = g->work;
     const int64_t n = g->n, nwords = (n + 31) / 32;
     EdgeMapArgs a;
@@ -209,6 +209,7 @@ kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, in
     a.warp_max_edges = g->tuning.warp_max_edges;
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;
+    a.count_relaxed = count_relaxed;
     int bps = 0;
     int grid = edgemap_max_grid(lanes, g->lam_bits, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "edge-map: no resident launch shape (occupancy query failed)");
@@ -225,6 +226,7 @@ kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, in
     g->last_kernel_ms += ms;
     *res = *w.ctr_host;
     if (res->err == KERR_BARRIER_TIMEOUT) return fail(KAIROS_ERR_TIMEOUT, "edge-map: a grid barrier wait ran past its limit");
+    if (res->err == KERR_WAIT_TIMEOUT) return fail(KAIROS_ERR_TIMEOUT, "edge-map: a wait for a published chunk ran past its limit");
     if (res->err == KERR_ROUNDS) return fail(KAIROS_ERR_TIMEOUT, "edge-map: round cap (n + 1) reached");
     if (res->err) return fail(KAIROS_ERR_INTERNAL, "edge-map: split-range capacity exceeded");
     return KAIROS_OK;
@@ -268,7 +270,7 @@ kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_
                 }
             }
             EdgeMapCtr res;
-            st = run_launch(g, csr, lp, lanes, o, n, alias, &res);
+            st = run_launch(g, csr, lp, lanes, o, n, alias, stats != nullptr, &res);
             if (st != KAIROS_OK) return st;
             if (out && !dev) {
                 for (int j = 0; j < k; ++j) {
@@ -347,8 +349,8 @@ kairos_status kairos_graph_build(const kairos_edge_list *el, const kairos_graph_
     const bool want_rev = !(opts && opts->skip_reverse);
     g->tuning.lanes = 1;
     g->tuning.blocks_per_sm = 0;
-    g->tuning.warp_max_edges = 4096;
-    g->tuning.chunk_edges = 2048;
+    g->tuning.warp_max_edges = 128;
+    g->tuning.chunk_edges = 512;
     g->tuning.dense_div = 16;
     auto bail = [&](kairos_status st) {
         kairos_graph_free(g);
@@ -506,8 +508,8 @@ kairos_status kairos_set_tuning(kairos_graph *g, const kairos_tuning *t) {
     if (!(L == 1 || L == 2 || L == 4 || L == 8 || L == 16 || L == 32))
         return fail(KAIROS_ERR_INVALID_ARG, "tuning: lanes must be 1, 2, 4, 8, 16 or 32");
     if (t->blocks_per_sm < 0 || t->blocks_per_sm > 32) return fail(KAIROS_ERR_INVALID_ARG, "tuning: blocks_per_sm in [0, 32]");
-    if (t->warp_max_edges < 32 || t->warp_max_edges > (1 << 24))
-        return fail(KAIROS_ERR_INVALID_ARG, "tuning: warp_max_edges in [32, 2^24]");
+    if (t->warp_max_edges < 32 || t->warp_max_edges > (1 << 16))
+        return fail(KAIROS_ERR_INVALID_ARG, "tuning: warp_max_edges in [32, 65536]");
     if (t->chunk_edges < 32 || t->chunk_edges % 32 || t->chunk_edges > (1 << 24))
         return fail(KAIROS_ERR_INVALID_ARG, "tuning: chunk_edges a multiple of 32 in [32, 2^24]");
     if (t->dense_div < 0) return fail(KAIROS_ERR_INVALID_ARG, "tuning: dense_div >= 0");
@@ -527,7 +529,7 @@ kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32
     kairos_tuning win = base;
     double win_ms = -1;
     const int lanes_set[] = {1, 2, 4, 8, 16, 32};
-    const int wmax_set[] = {1024, 4096, 16384};
+    const int wmax_set[] = {32, 128, 512};
     const int dense_set[] = {0, 16};
     for (int L : lanes_set) {
         for (int wm : wmax_set) {
@@ -578,5 +580,18 @@ const char *kairos_status_string(kairos_status s) {
 }
 
 double kairos_last_kernel_ms(const kairos_graph *g) { return g ? g->last_kernel_ms : 0.0; }
+
+int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uint32_t *frontier, uint32_t *chunks,
+                                  double *ms) {
+    if (!g || max_rounds < 0 || !g->work.ctr_host) return 0;
+    const EdgeMapCtr &c = *g->work.ctr_host;
+    const int r = (int)std::min<unsigned>(c.rounds, (unsigned)std::min(max_rounds, PROFILE_ROUNDS));
+    for (int i = 0; i < r; ++i) {
+        if (frontier) frontier[i] = c.round_frontier[i];
+        if (chunks) chunks[i] = c.round_chunks[i];
+        if (ms) ms[i] = (double)(c.round_ns[i + 1] - c.round_ns[i]) * 1e-6;
+    }
+    return r;
+}
 
 }  // extern "C"

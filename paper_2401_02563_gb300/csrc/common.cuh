@@ -20,9 +20,11 @@ constexpr int FENCE_SHIFT = 5;          // one fence key every 32 edges
 constexpr int FENCE_B = 1 << FENCE_SHIFT;
 constexpr int EM_THREADS = 256;         // edge-map block size
 constexpr int MAX_LANES = 32;
+constexpr int PROFILE_ROUNDS = 256;
 
 // Device-side error codes reported through EdgeMapCtr::err.
-enum : int { KERR_NONE = 0, KERR_BARRIER_TIMEOUT = 1, KERR_ROUNDS = 2, KERR_CAPACITY = 3 };
+enum : int { KERR_NONE = 0, KERR_BARRIER_TIMEOUT = 1, KERR_ROUNDS = 2, KERR_CAPACITY = 3, KERR_WAIT_TIMEOUT = 4 };
+constexpr uint32_t NO_OWNER = 0xFFFFFFFFu;  // chunk_owner entry not yet published
 
 // ---- status / error plumbing ---------------------------------------------------------
 
@@ -59,19 +61,32 @@ struct Csr {
     int64_t max_deg = 0;
 };
 
-// Counters of one persistent edge-map launch (zeroed before each launch).
+// Counters of one persistent edge-map launch (zeroed before each launch).  Counters that
+// many warps update or poll in the same round sit on separate 128-byte lines.
+struct __align__(128) PaddedU32 {
+    unsigned int v;
+    unsigned int pad[31];
+};
+
 struct EdgeMapCtr {
     unsigned int bar_count;
     unsigned int bar_gen;
     int err;
     unsigned int rounds;
-    unsigned int qcount[3];     // frontier queue lengths, indexed by round mod 3
-    unsigned int bigcount[3];   // split ranges registered, by round mod 3
-    unsigned int chunks[3];     // grid-wide chunks registered, by round mod 3
-    unsigned int chunk_next[3]; // chunks claimed, by round mod 3
+    unsigned int pad0[28];
+    PaddedU32 qcount[3];     // frontier queue lengths, indexed by round mod 3
+    PaddedU32 bigcount[3];   // split ranges registered, by round mod 3
+    PaddedU32 chunks[3];     // grid-wide chunks registered, by round mod 3
+    PaddedU32 chunk_next[3]; // chunks claimed, by round mod 3
+    PaddedU32 bnext[3];      // frontier batches claimed, by round mod 3
+    PaddedU32 bdone[3];      // frontier batches finished, by round mod 3
     unsigned long long scanned;
     unsigned long long relaxed[MAX_LANES];
     unsigned int reached[MAX_LANES];
+    // per-round profile of the first PROFILE_ROUNDS rounds (block 0 after each barrier)
+    unsigned long long round_ns[PROFILE_ROUNDS + 1];
+    unsigned int round_frontier[PROFILE_ROUNDS];
+    unsigned int round_chunks[PROFILE_ROUNDS];
 };
 
 // A long per-vertex edge range split into grid-wide chunks.
@@ -79,6 +94,8 @@ struct BigEntry {
     uint64_t base;        // first edge index
     uint32_t len;         // edges in the range
     uint32_t chunk_base;  // first chunk id
+    uint32_t act;         // lanes with a non-empty departure interval
+    uint32_t pad;
 };
 
 // Per-lane query parameters of one launch (times already mirrored for latest departure).
@@ -119,6 +136,7 @@ struct EdgeMapArgs {
     LaneParams lanes;
     uint32_t max_rounds;
     int warp_max_edges, chunk_edges, dense_div;
+    int count_relaxed;     // nonzero: count relaxations per lane (query statistics)
 };
 
 // Launch one persistent edge-map (cooperative: every block resident).

@@ -17,11 +17,15 @@
 // at or after min_q thr and the end of the window by binary search (fence keys, then one
 // 32-edge block); an unindexed vertex scans its whole list, filtering by time.
 //
-// Work shapes: a warp takes 32 frontier vertices, gathers their lane states, computes
-// their edge ranges, and walks the concatenated ranges 32 edges at a time (coalesced
-// loads, a shuffle per lane group to share each edge with its W lanes).  Ranges longer
-// than warp_max_edges are cut into chunk_edges chunks that every warp of the grid claims
-// after a grid barrier.  Large frontiers are swept from the bitmap in vertex order.
+// Work shapes: a warp takes 32 frontier vertices and gathers their W lane states with
+// coalesced row loads (thread per lane), keeping per vertex the mask of lanes with work.
+// Edges are then thread-per-edge, K_EDGES independent edges per thread per step (coalesced
+// loads, several misses in flight), each looping over its source's active lanes only.
+// Ranges up to warp_max_edges are walked by the warp that found them, concatenated;
+// longer ones are cut into chunk_edges chunks.  Within a round, warps claim batches of 32
+// frontier vertices from a counter and, once none is left, claim chunks as they are
+// published (release/acquire on the chunk's owner word), so one grid barrier ends the
+// round.  Large frontiers are swept from the bitmap in vertex order.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -32,10 +36,22 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr unsigned long long BARRIER_SPIN_LIMIT = 1ull << 24;  // with 128 ns sleeps: > 2 s
 
+constexpr unsigned long long WAIT_SPIN_LIMIT = 1ull << 24;     // chunk publication waits
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Grid-wide barrier of a cooperative launch (all blocks resident).  Every wait is bounded:
@@ -99,9 +115,11 @@ template <int W>
 struct WarpSmem {
     uint32_t thr[32][W];  // per slot and lane: first departure to scan
     uint32_t lim[32][W];  // per slot and lane: scan below this departure
+    uint32_t act[32];     // per slot: lanes whose interval [thr, lim) is non-empty
     uint64_t base[32];    // per slot: first edge of its range
     uint32_t start[32];   // per slot: exclusive prefix of range lengths
     uint32_t L[32], H[32];
+    uint32_t bthr[W], blim[W];  // lane bounds of the split range being walked
 };
 
 // Per-thread constants of its query lane q = lane % W.
@@ -112,7 +130,15 @@ struct LaneReg {
     int32_t src;
 };
 
-// Warp-aggregated append of the lanes with `need` to the next frontier queue.
+struct BlockSmem {
+    uint32_t tw[MAX_LANES];   // window end per lane
+    uint32_t cnt[MAX_LANES];  // relaxations per lane (lanes > 1)
+    int flag;
+};
+
+constexpr int K_EDGES = 4;  // independent edges per thread per step
+
+// Warp-aggregated append of the threads with `need` to the next frontier queue.
 __device__ __forceinline__ void frontier_append(bool need, int32_t v, int lane, int32_t *queue, unsigned *count) {
     const unsigned mask = __ballot_sync(FULL, need);
     if (mask) {
@@ -124,48 +150,97 @@ __device__ __forceinline__ void frontier_append(bool need, int32_t v, int lane, 
     }
 }
 
-// Relax the 32 edges held one per thread (d < 0: none) for every lane: edge k*G + grp is
-// taken by the W threads of group grp, thread q deciding for lane q with bounds thr/lim.
-template <int W, typename BoundsF>
-__device__ __forceinline__ void relax_edges(const EdgeMapArgs &a, const LaneReg &R, int lane, int32_t d, uint32_t tt,
-                                            uint32_t ll, int slot, BoundsF bounds, int nxt, int n3,
-                                            unsigned long long &relaxed) {
-    constexpr int G = 32 / W;
+// Lower the label of v in lane q to tau; true when v newly enters the next frontier.
+template <int W>
+__device__ __forceinline__ bool improve(const EdgeMapArgs &a, int32_t v, int q, uint32_t tau, uint32_t cur, int nxt) {
+    if (!(tau < cur)) return false;
+    const uint32_t old = atomicMin(a.arr + (size_t)v * W + q, tau);
+    if (!(tau < old)) return false;
+    const uint32_t bit = 1u << (v & 31);
+    return !(atomicOr(&a.bm[nxt][v >> 5], bit) & bit);
+}
+
+// Relax K edges per thread (d < 0: none).  Edge k of this thread comes from a slot whose
+// active lanes are act(k) and whose bounds for lane q are bounds(k, q, thr, lim).
+template <int W, typename ActF, typename BoundsF>
+__device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)[K_EDGES], const uint32_t (&tt)[K_EDGES],
+                                        const uint32_t (&ll)[K_EDGES], ActF actf, BoundsF bounds, BlockSmem &B,
+                                        unsigned long long &cnt1, int lane, int nxt, int n3) {
+    if constexpr (W == 1) {
+        bool ok[K_EDGES];
+        uint32_t cur[K_EDGES];
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
-        const int ei = k * G + R.grp;
-        const int32_t dv = (W == 1) ? d : __shfl_sync(FULL, d, ei);
-        const uint32_t tv = (W == 1) ? tt : __shfl_sync(FULL, tt, ei);
-        const uint32_t lv = (W == 1) ? ll : __shfl_sync(FULL, ll, ei);
-        const int sl = (W == 1) ? slot : __shfl_sync(FULL, slot, ei);
-        bool need = false;
-        if (dv >= 0) {
+        for (int k = 0; k < K_EDGES; ++k) {
             uint32_t th, li;
-            bounds(sl, th, li);
-            if (th <= tv && tv < li) {
-                const uint32_t tau = tv + lv;  // <= TMAX: checked at graph build
-                if (tau <= R.tw) {
-                    ++relaxed;
-                    uint32_t *p = a.arr + (size_t)dv * W + R.q;
-                    if (tau < __ldcg(p)) {
-                        const uint32_t old = atomicMin(p, tau);
-                        if (tau < old) {
-                            const uint32_t bit = 1u << (dv & 31);
-                            const uint32_t ob = atomicOr(&a.bm[nxt][dv >> 5], bit);
-                            need = !(ob & bit);
+            bounds(k, 0, th, li);
+            ok[k] = d[k] >= 0 && actf(k) && th <= tt[k] && tt[k] < li && tt[k] + ll[k] <= B.tw[0];
+            cnt1 += ok[k];  // a register add: kept even when statistics are not requested
+        }
+#pragma unroll
+        for (int k = 0; k < K_EDGES; ++k) cur[k] = ok[k] ? __ldcg(a.arr + d[k]) : 0u;
+#pragma unroll
+        for (int k = 0; k < K_EDGES; ++k) {
+            const bool need = ok[k] && improve<1>(a, d[k], 0, tt[k] + ll[k], cur[k], nxt);
+            frontier_append(need, d[k], lane, a.queue[nxt], &a.ctr->qcount[n3].v);
+        }
+    } else {
+        // candidate lanes of each edge from the time bounds alone (shared memory), then the
+        // head's state-row segments holding them, fetched with independent vector loads
+        constexpr int SEG = (W >= 4) ? 4 : W;  // lanes per load
+        constexpr int NSEG = W / SEG;
+        constexpr uint32_t SEGMASK = (SEG == 32) ? 0xFFFFFFFFu : ((1u << SEG) - 1u);
+#pragma unroll
+        for (int k = 0; k < K_EDGES; ++k) {
+            uint32_t cand = 0;
+            const uint32_t tau = tt[k] + ll[k];
+            if (d[k] >= 0) {
+                uint32_t act = actf(k);
+                while (act) {
+                    const int q = __ffs(act) - 1;
+                    act &= act - 1;
+                    uint32_t th, li;
+                    bounds(k, q, th, li);
+                    if (th <= tt[k] && tt[k] < li && tau <= B.tw[q]) cand |= 1u << q;
+                }
+                if (a.count_relaxed)
+                    for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicAdd(&B.cnt[__ffs(c2) - 1], 1u);
+            }
+            bool need = false;
+            if (cand) {
+                const uint32_t *row = a.arr + (size_t)d[k] * W;
+                uint32_t cur[W];
+#pragma unroll
+                for (int sg = 0; sg < NSEG; ++sg) {
+                    if ((cand >> (sg * SEG)) & SEGMASK) {
+                        if constexpr (SEG == 4) {
+                            const uint4 v = *reinterpret_cast<const uint4 *>(row + sg * 4);  // may be stale: never below
+                            cur[sg * 4] = v.x;
+                            cur[sg * 4 + 1] = v.y;
+                            cur[sg * 4 + 2] = v.z;
+                            cur[sg * 4 + 3] = v.w;
+                        } else {
+                            const uint2 v = *reinterpret_cast<const uint2 *>(row);
+                            cur[0] = v.x;
+                            cur[1] = v.y;
                         }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < SEG; ++j) cur[sg * SEG + j] = 0u;
                     }
                 }
+#pragma unroll
+                for (int q = 0; q < W; ++q)
+                    if (((cand >> q) & 1u) && tau < cur[q]) need |= improve<W>(a, d[k], q, tau, cur[q], nxt);
             }
+            frontier_append(need, d[k], lane, a.queue[nxt], &a.ctr->qcount[n3].v);
         }
-        frontier_append(need, dv, lane, a.queue[nxt], &a.ctr->qcount[n3]);
     }
 }
 
 // Expand up to 32 frontier vertices (one per thread, u < 0 for none).
 template <int W, typename LamT>
-__device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, const LaneReg &R, int lane, int32_t u,
-                                       int nxt, int c3, int n3, unsigned long long &relaxed,
+__device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, BlockSmem &B, const LaneReg &R, int lane,
+                                       int32_t u, int nxt, int c3, int n3, unsigned long long &cnt1,
                                        unsigned long long &scanned) {
     const LamT *__restrict__ lam = (const LamT *)a.lam;
     // 1. lane states of the 32 slots: thread (k, lane) handles slot (32k + lane) / W, lane q
@@ -190,6 +265,7 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, con
         }
         S.thr[j][R.q] = th;
         S.lim[j][R.q] = li;
+        const unsigned on = __ballot_sync(FULL, th < li);
         uint32_t mn = th, mx = li;
 #pragma unroll
         for (int o = 1; o < W; o <<= 1) {
@@ -199,10 +275,12 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, con
         if (R.q == 0) {
             S.L[j] = mn;
             S.H[j] = mx;
+            S.act[j] = (W == 32) ? on : ((on >> (lane & ~(W - 1))) & ((1u << W) - 1u));
         }
     }
     __syncwarp();
-    // 2. edge range of slot `lane`
+    // 2. edge range of slot `lane`: [lower_bound(min thr), lower_bound(max lim)) when the
+    // vertex is indexed, its whole list otherwise
     uint32_t len = 0;
     uint64_t base = 0;
     const uint32_t Lm = S.L[lane], Hm = S.H[lane];
@@ -218,67 +296,91 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, con
         len = hi - lo;
         base = o0 + lo;
     }
-    // 3. long ranges go to the grid-wide chunk list
-    if (len > (uint32_t)a.warp_max_edges) {
+    // 3. ranges longer than warp_max_edges go to the grid-wide chunk list (one pair of
+    // atomics per warp)
+    const bool isbig = len > (uint32_t)a.warp_max_edges;
+    const unsigned bmask = __ballot_sync(FULL, isbig);
+    if (bmask) {
         const uint32_t CH = (uint32_t)a.chunk_edges;
-        const uint32_t nch = (len + CH - 1) / CH;
-        const uint32_t e = atomicAdd(&a.ctr->bigcount[c3], 1u);
-        const uint32_t cb = atomicAdd(&a.ctr->chunks[c3], nch);
-        if (e < a.cap_big && (uint64_t)cb + nch <= a.cap_chunks) {
-            a.big[e].base = base;
-            a.big[e].len = len;
-            a.big[e].chunk_base = cb;
-            for (int qq = 0; qq < W; ++qq) {
-                a.bigb[((size_t)e * W + qq) * 2] = S.thr[lane][qq];
-                a.bigb[((size_t)e * W + qq) * 2 + 1] = S.lim[lane][qq];
-            }
-            for (uint32_t c = 0; c < nch; ++c) a.chunk_owner[cb + c] = e;
-        } else {
-            atomicCAS(&a.ctr->err, 0, KERR_CAPACITY);
+        const uint32_t nch = isbig ? (len + CH - 1) / CH : 0u;
+        const uint32_t chincl = warp_incl_scan(nch, lane);
+        const uint32_t chtot = __shfl_sync(FULL, chincl, 31);
+        unsigned e0 = 0, c0 = 0;
+        if (lane == 0) {
+            e0 = atomicAdd(&a.ctr->bigcount[c3].v, (unsigned)__popc(bmask));
+            c0 = atomicAdd(&a.ctr->chunks[c3].v, chtot);
         }
-        len = 0;
+        e0 = __shfl_sync(FULL, e0, 0);
+        c0 = __shfl_sync(FULL, c0, 0);
+        if (isbig) {
+            const uint32_t e = e0 + __popc(bmask & ((1u << lane) - 1u));
+            const uint32_t cb = c0 + chincl - nch;
+            if (e < a.cap_big && (uint64_t)cb + nch <= a.cap_chunks) {
+                BigEntry be;
+                be.base = base;
+                be.len = len;
+                be.chunk_base = cb;
+                be.act = S.act[lane];
+                be.pad = 0;
+                a.big[e] = be;
+                for (int qq = 0; qq < W; ++qq) {
+                    a.bigb[((size_t)e * W + qq) * 2] = S.thr[lane][qq];
+                    a.bigb[((size_t)e * W + qq) * 2 + 1] = S.lim[lane][qq];
+                }
+                __threadfence();  // the entry is visible before any chunk names it
+                for (uint32_t c = 0; c < nch; ++c) st_release(&a.chunk_owner[cb + c], e);
+            } else {
+                atomicCAS(&a.ctr->err, 0, KERR_CAPACITY);
+            }
+            len = 0;
+        }
     }
-    // 4. walk the concatenated short ranges, 32 edges at a time
+    // 4. walk the concatenated short ranges, K_EDGES x 32 edges per step
     const uint32_t incl = warp_incl_scan(len, lane);
     const uint32_t T = __shfl_sync(FULL, incl, 31);
     S.start[lane] = incl - len;
     S.base[lane] = base;
     __syncwarp();
-    for (uint32_t c = 0; c < T; c += 32) {
-        const uint32_t item = c + lane;
-        int32_t d = -1;
-        uint32_t tt = 0, ll = 0;
-        int slot = 0;
-        if (item < T) {
-            int j = 0;
+    for (uint32_t c = 0; c < T; c += 32 * K_EDGES) {
+        int32_t d[K_EDGES];
+        uint32_t tt[K_EDGES], ll[K_EDGES];
+        int sl[K_EDGES];
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1)
-                if (S.start[j + step] <= item) j += step;
-            slot = j;
-            const uint64_t e = S.base[j] + (item - S.start[j]);
-            d = __ldg(&a.dst[e]);
-            tt = __ldg(&a.t[e]);
-            ll = (uint32_t)__ldg(&lam[e]);
-            ++scanned;
+        for (int k = 0; k < K_EDGES; ++k) {
+            const uint32_t item = c + k * 32 + lane;
+            d[k] = -1;
+            tt[k] = 0;
+            ll[k] = 0;
+            sl[k] = 0;
+            if (item < T) {
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (S.start[j + step] <= item) j += step;
+                sl[k] = j;
+                const uint64_t e = S.base[j] + (item - S.start[j]);
+                d[k] = __ldg(&a.dst[e]);
+                tt[k] = __ldg(&a.t[e]);
+                ll[k] = (uint32_t)__ldg(&lam[e]);
+                ++scanned;
+            }
         }
-        relax_edges<W>(a, R, lane, d, tt, ll, slot,
-                       [&](int sl, uint32_t &th, uint32_t &li) {
-                           th = S.thr[sl][R.q];
-                           li = S.lim[sl][R.q];
-                       },
-                       nxt, n3, relaxed);
+        relax_k<W>(a, d, tt, ll, [&](int k) { return S.act[sl[k]]; },
+                   [&](int k, int q, uint32_t &th, uint32_t &li) {
+                       th = S.thr[sl[k]][q];
+                       li = S.lim[sl[k]][q];
+                   },
+                   B, cnt1, lane, nxt, n3);
     }
     __syncwarp();
 }
 
 template <int W, typename LamT>
-__global__ void __launch_bounds__(EM_THREADS, 2) edgemap_kernel(const EdgeMapArgs a) {
+__global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(const EdgeMapArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_flag;
+    __shared__ BlockSmem B;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     WarpSmem<W> &S = reinterpret_cast<WarpSmem<W> *>(smem_raw)[wib];
-    const unsigned gw = blockIdx.x * (EM_THREADS / 32) + wib;
-    const unsigned nw = gridDim.x * (EM_THREADS / 32);
     const size_t tid = (size_t)blockIdx.x * EM_THREADS + threadIdx.x;
     const size_t nthr = (size_t)gridDim.x * EM_THREADS;
     const int64_t n = a.n;
@@ -294,7 +396,11 @@ __global__ void __launch_bounds__(EM_THREADS, 2) edgemap_kernel(const EdgeMapArg
     R.lim_cap = R.tw + 1u;
     R.strict = (a.lanes.strict_mask >> R.q) & 1u;
     R.src = a.lanes.src[R.q];
-    unsigned long long relaxed = 0, scanned = 0;
+    if (threadIdx.x < MAX_LANES) {
+        B.tw[threadIdx.x] = a.lanes.tw[threadIdx.x];
+        B.cnt[threadIdx.x] = 0;
+    }
+    unsigned long long cnt1 = 0, scanned = 0;
     unsigned reached = 0;
 
     // ---- initial labels (Alg. 2: t[x] = window start, t[v] = infinity) ----
@@ -306,110 +412,181 @@ __global__ void __launch_bounds__(EM_THREADS, 2) edgemap_kernel(const EdgeMapArg
         a.bm[0][i] = 0u;
         a.bm[1][i] = 0u;
     }
-    if (!grid_sync(C, &s_flag)) return;
+    if (!grid_sync(C, &B.flag)) return;
     if (blockIdx.x == 0 && threadIdx.x < (unsigned)a.lanes.nlanes) {
         const int qq = threadIdx.x;
         const int32_t s = a.lanes.src[qq];
         a.arr[(size_t)s * W + qq] = a.lanes.ta[qq];
         const uint32_t bit = 1u << (s & 31);
         const uint32_t old = atomicOr(&a.bm[0][s >> 5], bit);
-        if (!(old & bit)) a.queue[0][atomicAdd(&C->qcount[0], 1u)] = s;
+        if (!(old & bit)) a.queue[0][atomicAdd(&C->qcount[0].v, 1u)] = s;
     }
-    if (!grid_sync(C, &s_flag)) return;
+    if (!grid_sync(C, &B.flag)) return;
 
     // ---- rounds ----
     unsigned r = 0;
     for (;; ++r) {
         const int cur = r & 1, nxt = cur ^ 1;
         const int c3 = r % 3, n3 = (r + 1) % 3, p3 = (r + 2) % 3;
-        const unsigned F = __ldcg(&C->qcount[c3]);
+        const unsigned F = __ldcg(&C->qcount[c3].v);
+        if (tid == 0 && r <= PROFILE_ROUNDS) {
+            C->round_ns[r] = globaltimer();
+            if (r > 0) C->round_chunks[r - 1] = __ldcg(&C->chunks[(r + 2) % 3].v);
+            if (r < PROFILE_ROUNDS) C->round_frontier[r] = F;
+        }
         if (F == 0) break;
         if (r >= a.max_rounds) {
             if (tid == 0) atomicCAS(&C->err, 0, KERR_ROUNDS);
             break;
         }
         if (tid == 0) {
-            C->qcount[p3] = 0;
-            C->bigcount[n3] = 0;
-            C->chunks[n3] = 0;
-            C->chunk_next[n3] = 0;
+            C->qcount[p3].v = 0;
+            C->bigcount[n3].v = 0;
+            C->chunks[n3].v = 0;
+            C->chunk_next[n3].v = 0;
+            C->bnext[n3].v = 0;
+            C->bdone[n3].v = 0;
         }
         const bool dense = a.dense_div > 0 && (int64_t)F * a.dense_div > n;
-        if (!dense) {
-            for (unsigned b = gw * 32; b < F; b += nw * 32) {
-                const unsigned i = b + lane;
-                const int32_t u = (i < F) ? __ldcg(&a.queue[cur][i]) : -1;
-                if (u >= 0) atomicAnd(&a.bm[cur][u >> 5], ~(1u << (u & 31)));
-                expand<W, LamT>(a, S, R, lane, u, nxt, c3, n3, relaxed, scanned);
-            }
-        } else {
-            // sweep the bitmap in vertex order; ballot-compact each 1024-vertex stripe
-            for (size_t wb = (size_t)gw * 32; wb < nwords; wb += (size_t)nw * 32) {
-                const size_t w = wb + lane;
-                const uint32_t bits = (w < nwords) ? __ldcg(&a.bm[cur][w]) : 0u;
-                if (bits) a.bm[cur][w] = 0u;
-                const uint32_t cnt = __popc(bits);
-                const uint32_t incl = warp_incl_scan(cnt, lane);
-                const uint32_t pre = incl - cnt;
-                const uint32_t total = __shfl_sync(FULL, incl, 31);
-                for (uint32_t b = 0; b < total; b += 32) {
-                    const uint32_t k = b + lane;
-                    int j = 0;
+        // work of the round: batches of 32 queued vertices (or 1024-vertex bitmap stripes),
+        // then the chunks that expanding them registered; both claimed dynamically
+        const unsigned nb = dense ? (unsigned)((nwords + 31) / 32) : (F + 31) / 32;
+        for (;;) {
+            unsigned b = nb;
+            if (lane == 0 && __ldcg(&C->bnext[c3].v) < nb) b = atomicAdd(&C->bnext[c3].v, 1u);
+            b = __shfl_sync(FULL, b, 0);
+            if (b < nb) {
+                if (!dense) {
+                    const unsigned i = b * 32 + lane;
+                    const int32_t u = (i < F) ? __ldcg(&a.queue[cur][i]) : -1;
+                    if (u >= 0) atomicAnd(&a.bm[cur][u >> 5], ~(1u << (u & 31)));
+                    expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned);
+                } else {
+                    // ballot-compact the 1024-vertex stripe, 32 vertices at a time
+                    const size_t wb = (size_t)b * 32;
+                    const size_t w = wb + lane;
+                    const uint32_t bits = (w < nwords) ? __ldcg(&a.bm[cur][w]) : 0u;
+                    if (bits) a.bm[cur][w] = 0u;
+                    const uint32_t cnt = __popc(bits);
+                    const uint32_t incl = warp_incl_scan(cnt, lane);
+                    const uint32_t pre = incl - cnt;
+                    const uint32_t total = __shfl_sync(FULL, incl, 31);
+                    for (uint32_t b2 = 0; b2 < total; b2 += 32) {
+                        const uint32_t k = b2 + lane;
+                        int j = 0;
 #pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const uint32_t pj = __shfl_sync(FULL, pre, j + step);
-                        if (pj <= k) j += step;
+                        for (int step = 16; step >= 1; step >>= 1) {
+                            const uint32_t pj = __shfl_sync(FULL, pre, j + step);
+                            if (pj <= k) j += step;
+                        }
+                        const uint32_t bj = __shfl_sync(FULL, bits, j);
+                        const uint32_t pj = __shfl_sync(FULL, pre, j);
+                        int32_t u = -1;
+                        if (k < total) u = (int32_t)((wb + j) * 32 + __fns(bj, 0, (int)(k - pj) + 1));
+                        expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned);
                     }
-                    const uint32_t bj = __shfl_sync(FULL, bits, j);
-                    const uint32_t pj = __shfl_sync(FULL, pre, j);
-                    int32_t u = -1;
-                    if (k < total) u = (int32_t)((wb + j) * 32 + __fns(bj, 0, (int)(k - pj) + 1));
-                    expand<W, LamT>(a, S, R, lane, u, nxt, c3, n3, relaxed, scanned);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();  // chunk registrations of this batch precede its completion
+                    atomicAdd(&C->bdone[c3].v, 1u);
+                }
+                continue;
+            }
+            // all batches are claimed: take the next chunk id, waiting (bounded) until it is
+            // published, or until every batch is done and no chunk has that id
+            unsigned c = 0, e = NO_OWNER;
+            int state = 0;  // 0 wait, 1 work, 2 no more work
+            if (lane == 0) {
+                // no claim while every registered chunk is taken and no batch can add more
+                unsigned backoff = 32;
+                unsigned long long spins = 0;
+                for (;;) {
+                    const unsigned have = __ldcg(&C->chunks[c3].v);
+                    if (__ldcg(&C->chunk_next[c3].v) < have) break;
+                    if (ld_acquire(&C->bdone[c3].v) >= nb && __ldcg(&C->chunk_next[c3].v) >= __ldcg(&C->chunks[c3].v)) {
+                        state = 2;
+                        break;
+                    }
+                    if (__ldcg(&C->err) != 0 || ++spins > WAIT_SPIN_LIMIT) {
+                        if (spins > WAIT_SPIN_LIMIT) atomicCAS(&C->err, 0, KERR_WAIT_TIMEOUT);
+                        state = 2;
+                        break;
+                    }
+                    __nanosleep(backoff);
+                    backoff = backoff < 1024 ? 2 * backoff : 1024;
+                }
+                if (state == 0) c = atomicAdd(&C->chunk_next[c3].v, 1u);
+                while (state == 0) {
+                    if (c < __ldcg(&C->chunks[c3].v) && c < a.cap_chunks) {
+                        e = ld_acquire(&a.chunk_owner[c]);
+                        if (e != NO_OWNER) {
+                            state = 1;
+                            break;
+                        }
+                    } else if (ld_acquire(&C->bdone[c3].v) >= nb && c >= __ldcg(&C->chunks[c3].v)) {
+                        state = 2;
+                        break;
+                    }
+                    if (__ldcg(&C->err) != 0) {
+                        state = 2;
+                        break;
+                    }
+                    if (++spins > WAIT_SPIN_LIMIT) {
+                        atomicCAS(&C->err, 0, KERR_WAIT_TIMEOUT);
+                        state = 2;
+                        break;
+                    }
+                    __nanosleep(backoff);
+                    backoff = backoff < 1024 ? 2 * backoff : 1024;
                 }
             }
-        }
-        if (!grid_sync(C, &s_flag)) return;
-
-        // split ranges: every warp claims chunks
-        const unsigned nch = __ldcg(&C->chunks[c3]);
-        if (nch > 0) {
-            for (;;) {
-                unsigned c = 0;
-                if (lane == 0) c = atomicAdd(&C->chunk_next[c3], 1u);
-                c = __shfl_sync(FULL, c, 0);
-                if (c >= nch || c >= a.cap_chunks) break;
-                const uint32_t e = __ldcg(&a.chunk_owner[c]);
-                if (e >= a.cap_big) continue;
-                const uint64_t bbase = __ldcg((const unsigned long long *)&a.big[e].base);
-                const uint32_t blen = __ldcg(&a.big[e].len);
-                const uint32_t bcb = __ldcg(&a.big[e].chunk_base);
-                if (c < bcb) continue;
-                const uint32_t st = (c - bcb) * (uint32_t)a.chunk_edges;
-                if (st >= blen) continue;
-                const uint32_t cnt = min((uint32_t)a.chunk_edges, blen - st);
-                const uint32_t th = __ldcg(&a.bigb[((size_t)e * W + R.q) * 2]);
-                const uint32_t li = __ldcg(&a.bigb[((size_t)e * W + R.q) * 2 + 1]);
-                for (uint32_t i = 0; i < cnt; i += 32) {
-                    const uint32_t item = i + lane;
-                    int32_t d = -1;
-                    uint32_t tt = 0, ll = 0;
+            state = __shfl_sync(FULL, state, 0);
+            if (state == 2) break;
+            c = __shfl_sync(FULL, c, 0);
+            e = __shfl_sync(FULL, e, 0);
+            if (lane == 0) a.chunk_owner[c] = NO_OWNER;  // free the id for the next round
+            if (e >= a.cap_big) continue;
+            const uint64_t bbase = __ldcg((const unsigned long long *)&a.big[e].base);
+            const uint32_t blen = __ldcg(&a.big[e].len);
+            const uint32_t bcb = __ldcg(&a.big[e].chunk_base);
+            const uint32_t bact = __ldcg(&a.big[e].act);
+            if (c < bcb) continue;
+            const uint32_t st = (c - bcb) * (uint32_t)a.chunk_edges;
+            if (st >= blen) continue;
+            const uint32_t cnt = min((uint32_t)a.chunk_edges, blen - st);
+            if (lane < W) {
+                S.bthr[lane] = __ldcg(&a.bigb[((size_t)e * W + lane) * 2]);
+                S.blim[lane] = __ldcg(&a.bigb[((size_t)e * W + lane) * 2 + 1]);
+            }
+            __syncwarp();
+            for (uint32_t i = 0; i < cnt; i += 32 * K_EDGES) {
+                int32_t d[K_EDGES];
+                uint32_t tt[K_EDGES], ll[K_EDGES];
+#pragma unroll
+                for (int k = 0; k < K_EDGES; ++k) {
+                    const uint32_t item = i + k * 32 + lane;
+                    d[k] = -1;
+                    tt[k] = 0;
+                    ll[k] = 0;
                     if (item < cnt) {
                         const uint64_t ed = bbase + st + item;
-                        d = __ldg(&a.dst[ed]);
-                        tt = __ldg(&a.t[ed]);
-                        ll = (uint32_t)__ldg(&lam[ed]);
+                        d[k] = __ldg(&a.dst[ed]);
+                        tt[k] = __ldg(&a.t[ed]);
+                        ll[k] = (uint32_t)__ldg(&lam[ed]);
                         ++scanned;
                     }
-                    relax_edges<W>(a, R, lane, d, tt, ll, 0,
-                                   [&](int, uint32_t &x, uint32_t &y) {
-                                       x = th;
-                                       y = li;
-                                   },
-                                   nxt, n3, relaxed);
                 }
+                relax_k<W>(a, d, tt, ll, [&](int) { return bact; },
+                           [&](int, int q, uint32_t &th, uint32_t &li) {
+                               th = S.bthr[q];
+                               li = S.blim[q];
+                           },
+                           B, cnt1, lane, nxt, n3);
             }
-            if (!grid_sync(C, &s_flag)) return;
+            __syncwarp();
         }
+        if (!grid_sync(C, &B.flag)) return;
     }
 
     // ---- read out: out[row_q][v] = label (mirrored back for latest departure) ----
@@ -427,18 +604,21 @@ __global__ void __launch_bounds__(EM_THREADS, 2) edgemap_kernel(const EdgeMapArg
     }
     // ---- counters ----
 #pragma unroll
-    for (int o = W; o < 32; o <<= 1) {
-        relaxed += __shfl_xor_sync(FULL, relaxed, o);
-        reached += __shfl_xor_sync(FULL, reached, o);
-    }
+    for (int o = W; o < 32; o <<= 1) reached += __shfl_xor_sync(FULL, reached, o);
     unsigned long long sc = scanned;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) sc += __shfl_xor_sync(FULL, sc, o);
-    if (lane < W && R.on) {
-        atomicAdd(&C->relaxed[lane], relaxed);
-        atomicAdd(&C->reached[lane], reached);
+    for (int o = 1; o < 32; o <<= 1) {
+        sc += __shfl_xor_sync(FULL, sc, o);
+        cnt1 += __shfl_xor_sync(FULL, cnt1, o);
     }
+    if (lane < W && R.on) atomicAdd(&C->reached[lane], reached);
     if (lane == 0) atomicAdd(&C->scanned, sc);
+    if (W == 1) {
+        if (lane == 0) atomicAdd(&C->relaxed[0], cnt1);
+    } else {
+        __syncthreads();
+        if (threadIdx.x < (unsigned)a.lanes.nlanes) atomicAdd(&C->relaxed[threadIdx.x], (unsigned long long)B.cnt[threadIdx.x]);
+    }
     if (tid == 0) C->rounds = r;
 }
 

@@ -152,7 +152,7 @@ def test_work_shapes(tiny, warp_max, chunk, dense):
         want = orc.query(q)
         assert np.array_equal(got[i], want), q
         assert stats[i].relaxed_edges == orc.admissible(q, want)
-    g.set_tuning(lanes=1, warp_max_edges=4096, chunk_edges=2048, dense_div=16)
+    g.set_tuning(lanes=1, warp_max_edges=128, chunk_edges=512, dense_div=16)
 
 
 # ---- random multigraphs: zero durations, self-loops, parallel edges, ties -----------------
