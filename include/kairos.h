@@ -225,6 +225,12 @@ double kairos_last_kernel_ms(const kairos_graph *g);
 int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uint32_t *frontier, uint32_t *chunks,
                                   double *ms);
 
+/* Cycle counts of the last edge-map launch, summed over warps, for 8 phases: lane-state
+ * gather, range search, chunk registration, local walk, chunk wait, chunk walk, grid
+ * barrier, other.  Zero unless the process ran with KAIROS_PHASE_CLOCK=1 in its
+ * environment.  Returns 8, or 0 on a NULL argument.  Diagnostic only. */
+int32_t kairos_last_phase_cycles(const kairos_graph *g, uint64_t *cycles8);
+
 #ifdef __cplusplus
 }
 #endif

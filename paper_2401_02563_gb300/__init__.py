@@ -109,6 +109,7 @@ SIGNATURES = {
     "kairos_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "kairos_last_kernel_ms": (ctypes.c_double, [_P]),
     "kairos_last_round_profile": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P]),
+    "kairos_last_phase_cycles": (ctypes.c_int32, [_P, _P]),
 }
 
 
@@ -343,6 +344,18 @@ def kairos_last_error() -> str:
 
 def kairos_last_kernel_ms(g) -> float:
     return float(lib().kairos_last_kernel_ms(g))
+
+
+PHASES = ("lane states", "range search", "chunk registration", "local walk", "chunk wait", "chunk walk",
+          "grid barrier", "other")
+
+
+def kairos_last_phase_cycles(g):
+    """Per-phase cycles (summed over warps) of the last launch; zeros unless
+    KAIROS_PHASE_CLOCK=1 was set before the process started."""
+    c = np.zeros(8, np.uint64)
+    lib().kairos_last_phase_cycles(g, c.ctypes.data)
+    return dict(zip(PHASES, c.tolist()))
 
 
 def kairos_last_round_profile(g, max_rounds=256):

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -210,6 +211,8 @@ kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, in
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;
     a.count_relaxed = count_relaxed;
+    static const int phase_clock = getenv("KAIROS_PHASE_CLOCK") ? atoi(getenv("KAIROS_PHASE_CLOCK")) : 0;
+    a.phase_clock = phase_clock;
     int bps = 0;
     int grid = edgemap_max_grid(lanes, g->lam_bits, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "edge-map: no resident launch shape (occupancy query failed)");
@@ -592,6 +595,12 @@ int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uin
         if (ms) ms[i] = (double)(c.round_ns[i + 1] - c.round_ns[i]) * 1e-6;
     }
     return r;
+}
+
+int32_t kairos_last_phase_cycles(const kairos_graph *g, uint64_t *cycles8) {
+    if (!g || !cycles8 || !g->work.ctr_host) return 0;
+    for (int i = 0; i < 8; ++i) cycles8[i] = g->work.ctr_host->phase_cycles[i];
+    return 8;
 }
 
 }  // extern "C"

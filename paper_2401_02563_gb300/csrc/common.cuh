@@ -87,6 +87,10 @@ struct EdgeMapCtr {
     unsigned long long round_ns[PROFILE_ROUNDS + 1];
     unsigned int round_frontier[PROFILE_ROUNDS];
     unsigned int round_chunks[PROFILE_ROUNDS];
+    // SM cycles summed over warps per phase when EdgeMapArgs::phase_clock is set:
+    // 0 lane states, 1 range search, 2 chunk registration, 3 local walk, 4 chunk wait,
+    // 5 chunk walk, 6 grid barrier, 7 other
+    unsigned long long phase_cycles[8];
 };
 
 // A long per-vertex edge range split into grid-wide chunks.
@@ -137,6 +141,7 @@ struct EdgeMapArgs {
     uint32_t max_rounds;
     int warp_max_edges, chunk_edges, dense_div;
     int count_relaxed;     // nonzero: count relaxations per lane (query statistics)
+    int phase_clock;       // nonzero: accumulate per-phase cycle counts (diagnostics)
 };
 
 // Launch one persistent edge-map (cooperative: every block resident).

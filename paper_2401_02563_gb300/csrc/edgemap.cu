@@ -93,22 +93,41 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
     return x;
 }
 
-// First index i in [0, deg) with tl[i] >= x, through the fence keys F (F[k] = tl[32 k]).
-__device__ __forceinline__ uint32_t lower_bound_fenced(const uint32_t *__restrict__ tl, uint32_t deg,
-                                                       const uint32_t *__restrict__ F, uint32_t x) {
-    uint32_t lo = 0, hi = (deg + FENCE_B - 1) >> FENCE_SHIFT;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(&F[mid]) < x) lo = mid + 1; else hi = mid;
+// First indices i in [0, deg) with tl[i] >= x and with tl[i] >= y, through the fence keys
+// F (F[k] = tl[32 k]): a binary search over the fences, then one inside a 32-edge block.
+// The two searches are interleaved so that their loads are in flight together.
+__device__ __forceinline__ void lower_bound2_fenced(const uint32_t *__restrict__ tl, uint32_t deg,
+                                                    const uint32_t *__restrict__ F, uint32_t x, uint32_t y,
+                                                    uint32_t &rx, uint32_t &ry) {
+    const uint32_t nf = (deg + FENCE_B - 1) >> FENCE_SHIFT;
+    uint32_t lx = 0, hx = nf, ly = 0, hy = nf;
+    while (lx < hx || ly < hy) {
+        const uint32_t mx = (lx + hx) >> 1, my = (ly + hy) >> 1;
+        const uint32_t fx = lx < hx ? __ldg(&F[mx]) : 0u;
+        const uint32_t fy = ly < hy ? __ldg(&F[my]) : 0u;
+        if (lx < hx) {
+            if (fx < x) lx = mx + 1; else hx = mx;
+        }
+        if (ly < hy) {
+            if (fy < y) ly = my + 1; else hy = my;
+        }
     }
-    if (lo == 0) return 0;
-    const uint32_t b = (lo - 1) << FENCE_SHIFT;  // tl[b] < x
-    uint32_t l2 = b + 1, h2 = min(deg, b + FENCE_B);
-    while (l2 < h2) {
-        uint32_t mid = (l2 + h2) >> 1;
-        if (__ldg(&tl[mid]) < x) l2 = mid + 1; else h2 = mid;
+    // block b = k - 1 holds the answer in (32 b, min(32 b + 32, deg)]; k == 0 means 0
+    uint32_t bx = lx ? ((lx - 1) << FENCE_SHIFT) + 1 : 0, ex = lx ? min(deg, ((lx - 1) << FENCE_SHIFT) + FENCE_B) : 0;
+    uint32_t by = ly ? ((ly - 1) << FENCE_SHIFT) + 1 : 0, ey = ly ? min(deg, ((ly - 1) << FENCE_SHIFT) + FENCE_B) : 0;
+    while (bx < ex || by < ey) {
+        const uint32_t mx = (bx + ex) >> 1, my = (by + ey) >> 1;
+        const uint32_t tx = bx < ex ? __ldg(&tl[mx]) : 0u;
+        const uint32_t ty = by < ey ? __ldg(&tl[my]) : 0u;
+        if (bx < ex) {
+            if (tx < x) bx = mx + 1; else ex = mx;
+        }
+        if (by < ey) {
+            if (ty < y) by = my + 1; else ey = my;
+        }
     }
-    return l2;
+    rx = bx;
+    ry = by;
 }
 
 template <int W>
@@ -120,6 +139,29 @@ struct WarpSmem {
     uint32_t start[32];   // per slot: exclusive prefix of range lengths
     uint32_t L[32], H[32];
     uint32_t bthr[W], blim[W];  // lane bounds of the split range being walked
+    // the same bounds as sorted breakpoints: lanes {q : thr_q <= t < lim_q} = bmask[i]
+    // for bkey[i] <= t < bkey[i + 1] (bkey[-1] = -inf, mask 0)
+    uint32_t bkey[2 * W], bmask[2 * W];
+};
+
+// Per-warp phase timer (diagnostics): adds the cycles since the last mark to phase p.
+struct PhaseClock {
+    bool on;
+    long long last;
+    unsigned long long acc[8];
+    __device__ __forceinline__ void init(bool enable) {
+        on = enable;
+        last = on ? clock64() : 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = 0;
+    }
+    __device__ __forceinline__ void mark(int p) {
+        if (on) {
+            const long long now = clock64();
+            acc[p] += (unsigned long long)(now - last);
+            last = now;
+        }
+    }
 };
 
 // Per-thread constants of its query lane q = lane % W.
@@ -138,34 +180,112 @@ struct BlockSmem {
 
 constexpr int K_EDGES = 4;  // independent edges per thread per step
 
-// Warp-aggregated append of the threads with `need` to the next frontier queue.
-__device__ __forceinline__ void frontier_append(bool need, int32_t v, int lane, int32_t *queue, unsigned *count) {
-    const unsigned mask = __ballot_sync(FULL, need);
-    if (mask) {
-        const int leader = __ffs(mask) - 1;
-        unsigned base = 0;
-        if (lane == leader) base = atomicAdd(count, (unsigned)__popc(mask));
-        base = __shfl_sync(FULL, base, leader);
-        if (need) queue[base + __popc(mask & ((1u << lane) - 1u))] = v;
+// Sorted breakpoints of the lane intervals [thr_q, lim_q) of the chunk being walked, and
+// for each breakpoint the lanes whose interval contains it (so that for departure t the
+// candidate lanes are bmask[i] with bkey[i] <= t < bkey[i+1]).  Inactive lanes contribute
+// keys INF.  A bitonic sort of the 2W keys, W <= 32, two per thread.
+template <int W>
+__device__ __forceinline__ void build_breakpoints(WarpSmem<W> &S, int lane, uint32_t act) {
+    constexpr int N = 2 * W;  // keys; thread `lane` holds keys lane and lane + 32 when present
+    uint32_t k0 = INF, k1 = INF;
+    if (lane < W) {
+        const bool on = (act >> lane) & 1u;
+        k0 = on ? S.bthr[lane] : INF;
+        k1 = on ? S.blim[lane] : INF;
     }
+    // element index e = lane (k0) for e < 32 or lane + 32 (k1); with N <= 32 both live in
+    // k0 of lanes [0, N): rearrange so that element e sits in thread e % 32, slot e / 32
+    uint32_t x0, x1;
+    if constexpr (N <= 32) {
+        // element e: e < W -> thr of lane e, else lim of lane e - W
+        const uint32_t a0 = __shfl_sync(0xFFFFFFFFu, k0, lane % W);
+        const uint32_t a1 = __shfl_sync(0xFFFFFFFFu, k1, lane % W);
+        x0 = lane < W ? a0 : (lane < N ? a1 : INF);
+        x1 = INF;
+    } else {  // W == 32: thread lane holds thr (element lane) and lim (element lane + 32)
+        x0 = k0;
+        x1 = k1;
+    }
+    // bitonic sort of 64 slots (32 threads x 2), ascending by element index lane + 32 * slot
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 32) {  // partners are the two slots of the same thread
+                const bool up = (lane & size) == 0 || size == 64;
+                const uint32_t lo = min(x0, x1), hi = max(x0, x1);
+                x0 = up ? lo : hi;
+                x1 = up ? hi : lo;
+            } else {
+#pragma unroll
+                for (int slot = 0; slot < 2; ++slot) {
+                    uint32_t &x = slot ? x1 : x0;
+                    const int e = lane + 32 * slot;
+                    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, stride);
+                    const bool up = (e & size) == 0;
+                    const bool lower = (e & stride) == 0;
+                    x = (lower == up) ? min(x, y) : max(x, y);
+                }
+            }
+        }
+    }
+    // masks: lanes q with thr_q <= key < lim_q
+    if constexpr (N <= 32) {
+        if (lane < N) {
+            uint32_t m = 0;
+            for (int q = 0; q < W; ++q)
+                if (((act >> q) & 1u) && S.bthr[q] <= x0 && x0 < S.blim[q]) m |= 1u << q;
+            S.bkey[lane] = x0;
+            S.bmask[lane] = m;
+        }
+    } else {
+        uint32_t m0 = 0, m1 = 0;
+        for (int q = 0; q < W; ++q) {
+            if (!((act >> q) & 1u)) continue;
+            const uint32_t th = S.bthr[q], li = S.blim[q];
+            if (th <= x0 && x0 < li) m0 |= 1u << q;
+            if (th <= x1 && x1 < li) m1 |= 1u << q;
+        }
+        S.bkey[lane] = x0;
+        S.bmask[lane] = m0;
+        S.bkey[lane + 32] = x1;
+        S.bmask[lane + 32] = m1;
+    }
+    __syncwarp();
 }
 
-// Lower the label of v in lane q to tau; true when v newly enters the next frontier.
-template <int W>
-__device__ __forceinline__ bool improve(const EdgeMapArgs &a, int32_t v, int q, uint32_t tau, uint32_t cur, int nxt) {
-    if (!(tau < cur)) return false;
-    const uint32_t old = atomicMin(a.arr + (size_t)v * W + q, tau);
-    if (!(tau < old)) return false;
-    const uint32_t bit = 1u << (v & 31);
-    return !(atomicOr(&a.bm[nxt][v >> 5], bit) & bit);
+// Append the (up to K_EDGES) vertices this thread marked to the next frontier queue: one
+// warp-wide prefix sum and one atomic per warp.
+__device__ __forceinline__ void frontier_append_k(uint32_t needmask, const int32_t (&d)[K_EDGES], int lane,
+                                                  int32_t *queue, unsigned *count) {
+    const uint32_t c = __popc(needmask);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) return;
+    unsigned base = 0;
+    if (lane == 31) base = atomicAdd(count, total);
+    base = __shfl_sync(FULL, base, 31) + incl - c;
+#pragma unroll
+    for (int k = 0; k < K_EDGES; ++k)
+        if ((needmask >> k) & 1u) queue[base++] = d[k];
 }
 
 // Relax K edges per thread (d < 0: none).  Edge k of this thread comes from a slot whose
 // active lanes are act(k) and whose bounds for lane q are bounds(k, q, thr, lim).
+// A lane whose (possibly stale, never too low) copy of the head's label is above the
+// arrival issues a fire-and-forget atomic minimum; the head then gets one frontier-bitmap
+// test-and-set per edge.  A head marked although another thread lowered it first is
+// harmless: its next expansion finds every interval empty.
 template <int W, typename ActF, typename BoundsF>
 __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)[K_EDGES], const uint32_t (&tt)[K_EDGES],
                                         const uint32_t (&ll)[K_EDGES], ActF actf, BoundsF bounds, BlockSmem &B,
                                         unsigned long long &cnt1, int lane, int nxt, int n3) {
+    uint32_t mark = 0;  // bit k: edge k lowered its head in some lane
     if constexpr (W == 1) {
         bool ok[K_EDGES];
         uint32_t cur[K_EDGES];
@@ -180,12 +300,15 @@ __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)
         for (int k = 0; k < K_EDGES; ++k) cur[k] = ok[k] ? __ldcg(a.arr + d[k]) : 0u;
 #pragma unroll
         for (int k = 0; k < K_EDGES; ++k) {
-            const bool need = ok[k] && improve<1>(a, d[k], 0, tt[k] + ll[k], cur[k], nxt);
-            frontier_append(need, d[k], lane, a.queue[nxt], &a.ctr->qcount[n3].v);
+            const uint32_t tau = tt[k] + ll[k];
+            if (ok[k] && tau < cur[k]) {
+                atomicMin(a.arr + d[k], tau);  // result unused: a reduction
+                mark |= 1u << k;
+            }
         }
     } else {
-        // candidate lanes of each edge from the time bounds alone (shared memory), then the
-        // head's state-row segments holding them, fetched with independent vector loads
+        // candidate lanes of each edge from the time bounds, then the head's state-row
+        // segments holding them, fetched with independent vector loads
         constexpr int SEG = (W >= 4) ? 4 : W;  // lanes per load
         constexpr int NSEG = W / SEG;
         constexpr uint32_t SEGMASK = (SEG == 32) ? 0xFFFFFFFFu : ((1u << SEG) - 1u);
@@ -205,9 +328,8 @@ __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)
                 if (a.count_relaxed)
                     for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicAdd(&B.cnt[__ffs(c2) - 1], 1u);
             }
-            bool need = false;
             if (cand) {
-                const uint32_t *row = a.arr + (size_t)d[k] * W;
+                uint32_t *row = a.arr + (size_t)d[k] * W;
                 uint32_t cur[W];
 #pragma unroll
                 for (int sg = 0; sg < NSEG; ++sg) {
@@ -230,18 +352,30 @@ __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)
                 }
 #pragma unroll
                 for (int q = 0; q < W; ++q)
-                    if (((cand >> q) & 1u) && tau < cur[q]) need |= improve<W>(a, d[k], q, tau, cur[q], nxt);
+                    if (((cand >> q) & 1u) && tau < cur[q]) {
+                        atomicMin(row + q, tau);  // result unused: a reduction
+                        mark |= 1u << k;
+                    }
             }
-            frontier_append(need, d[k], lane, a.queue[nxt], &a.ctr->qcount[n3].v);
         }
     }
+    // one bitmap test-and-set per marked edge, all in flight together
+    uint32_t old[K_EDGES];
+#pragma unroll
+    for (int k = 0; k < K_EDGES; ++k)
+        old[k] = ((mark >> k) & 1u) ? atomicOr(&a.bm[nxt][d[k] >> 5], 1u << (d[k] & 31)) : 0xFFFFFFFFu;
+    uint32_t need = 0;
+#pragma unroll
+    for (int k = 0; k < K_EDGES; ++k)
+        if (!((old[k] >> (d[k] & 31)) & 1u)) need |= 1u << k;
+    frontier_append_k(need, d, lane, a.queue[nxt], &a.ctr->qcount[n3].v);
 }
 
 // Expand up to 32 frontier vertices (one per thread, u < 0 for none).
 template <int W, typename LamT>
 __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, BlockSmem &B, const LaneReg &R, int lane,
                                        int32_t u, int nxt, int c3, int n3, unsigned long long &cnt1,
-                                       unsigned long long &scanned) {
+                                       unsigned long long &scanned, PhaseClock &pc) {
     const LamT *__restrict__ lam = (const LamT *)a.lam;
     // 1. lane states of the 32 slots: thread (k, lane) handles slot (32k + lane) / W, lane q
 #pragma unroll
@@ -279,6 +413,7 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, Blo
         }
     }
     __syncwarp();
+    pc.mark(0);
     // 2. edge range of slot `lane`: [lower_bound(min thr), lower_bound(max lim)) when the
     // vertex is indexed, its whole list otherwise
     uint32_t len = 0;
@@ -289,13 +424,11 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, Blo
         const uint32_t deg = (uint32_t)(__ldg(&a.off[u + 1]) - o0);
         const uint32_t fi = a.fidx ? __ldg(&a.fidx[u]) : NO_FENCE;
         uint32_t lo = 0, hi = deg;
-        if (fi != NO_FENCE) {
-            lo = lower_bound_fenced(a.t + o0, deg, a.fence + fi, Lm);
-            hi = lower_bound_fenced(a.t + o0, deg, a.fence + fi, Hm);
-        }
+        if (fi != NO_FENCE) lower_bound2_fenced(a.t + o0, deg, a.fence + fi, Lm, Hm, lo, hi);
         len = hi - lo;
         base = o0 + lo;
     }
+    pc.mark(1);
     // 3. ranges longer than warp_max_edges go to the grid-wide chunk list (one pair of
     // atomics per warp)
     const bool isbig = len > (uint32_t)a.warp_max_edges;
@@ -335,6 +468,7 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, Blo
             len = 0;
         }
     }
+    pc.mark(2);
     // 4. walk the concatenated short ranges, K_EDGES x 32 edges per step
     const uint32_t incl = warp_incl_scan(len, lane);
     const uint32_t T = __shfl_sync(FULL, incl, 31);
@@ -373,6 +507,7 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, Blo
                    B, cnt1, lane, nxt, n3);
     }
     __syncwarp();
+    pc.mark(3);
 }
 
 template <int W, typename LamT>
@@ -402,6 +537,8 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
     }
     unsigned long long cnt1 = 0, scanned = 0;
     unsigned reached = 0;
+    PhaseClock pc;
+    pc.init(a.phase_clock != 0);
 
     // ---- initial labels (Alg. 2: t[x] = window start, t[v] = infinity) ----
     for (size_t i = tid; i < (size_t)n * W; i += nthr) {
@@ -460,7 +597,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                     const unsigned i = b * 32 + lane;
                     const int32_t u = (i < F) ? __ldcg(&a.queue[cur][i]) : -1;
                     if (u >= 0) atomicAnd(&a.bm[cur][u >> 5], ~(1u << (u & 31)));
-                    expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned);
+                    expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned, pc);
                 } else {
                     // ballot-compact the 1024-vertex stripe, 32 vertices at a time
                     const size_t wb = (size_t)b * 32;
@@ -483,7 +620,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                         const uint32_t pj = __shfl_sync(FULL, pre, j);
                         int32_t u = -1;
                         if (k < total) u = (int32_t)((wb + j) * 32 + __fns(bj, 0, (int)(k - pj) + 1));
-                        expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned);
+                        expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned, pc);
                     }
                 }
                 __syncwarp();
@@ -542,6 +679,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                 }
             }
             state = __shfl_sync(FULL, state, 0);
+            pc.mark(4);
             if (state == 2) break;
             c = __shfl_sync(FULL, c, 0);
             e = __shfl_sync(FULL, e, 0);
@@ -560,6 +698,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                 S.blim[lane] = __ldcg(&a.bigb[((size_t)e * W + lane) * 2 + 1]);
             }
             __syncwarp();
+            if (W > 1) build_breakpoints<W>(S, lane, bact);
             for (uint32_t i = 0; i < cnt; i += 32 * K_EDGES) {
                 int32_t d[K_EDGES];
                 uint32_t tt[K_EDGES], ll[K_EDGES];
@@ -577,16 +716,33 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                         ++scanned;
                     }
                 }
-                relax_k<W>(a, d, tt, ll, [&](int) { return bact; },
+                relax_k<W>(a, d, tt, ll,
+                           [&](int k) -> uint32_t {
+                               if (W == 1) return bact;
+                               int lo = 0, hi = 2 * W;  // first breakpoint above t
+                               while (lo < hi) {
+                                   const int mid = (lo + hi) >> 1;
+                                   if (S.bkey[mid] <= tt[k]) lo = mid + 1; else hi = mid;
+                               }
+                               return lo ? S.bmask[lo - 1] : 0u;
+                           },
                            [&](int, int q, uint32_t &th, uint32_t &li) {
-                               th = S.bthr[q];
-                               li = S.blim[q];
+                               if (W == 1) {
+                                   th = S.bthr[q];
+                                   li = S.blim[q];
+                               } else {  // the mask already holds exactly the lanes whose interval contains t
+                                   th = 0u;
+                                   li = INF;
+                               }
                            },
                            B, cnt1, lane, nxt, n3);
             }
             __syncwarp();
+            pc.mark(5);
         }
+        pc.mark(7);
         if (!grid_sync(C, &B.flag)) return;
+        pc.mark(6);
     }
 
     // ---- read out: out[row_q][v] = label (mirrored back for latest departure) ----
@@ -620,6 +776,10 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
         if (threadIdx.x < (unsigned)a.lanes.nlanes) atomicAdd(&C->relaxed[threadIdx.x], (unsigned long long)B.cnt[threadIdx.x]);
     }
     if (tid == 0) C->rounds = r;
+    pc.mark(7);
+    if (pc.on && lane == 0)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) atomicAdd(&C->phase_cycles[i], pc.acc[i]);
 }
 
 template <int W, typename LamT>
