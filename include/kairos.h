@@ -209,6 +209,28 @@ kairos_status kairos_serve_poll(kairos_server *s, uint64_t ticket, int64_t timeo
 /* Finish in-flight work, stop the thread and release the server.  NULL is ignored. */
 void kairos_serve_destroy(kairos_server *s);
 
+/* ---- query without device allocation ------------------------------------------------------ */
+
+/* Earliest arrival from src within [ta, tw] under Succeeds, like kairos_earliest_arrival,
+ * but allocating no device memory at all.  The paper has no counterpart: this serves
+ * callers that cannot allocate while they query, such as a process that hands all of
+ * its device memory to its own pool at start-up, or code called while another library
+ * captures a CUDA graph and forbids new allocations.  The graph itself must have been
+ * built beforehand (building allocates).
+ * out: uint32_t[n_vertices] in DEVICE memory, owned by the caller; it holds the labels
+ * throughout the query.  All other scratch lives in one fixed array compiled into the
+ * library (about 15.5 MB, held on every GPU that loads the library until the process
+ * exits) and limits the graph to at most 2^20 vertices, with its long adjacency ranges
+ * fitting 65536 split entries and 262144 chunks per round; larger graphs get
+ * INVALID_ARG with a message saying so.
+ * The first call on a device looks the array up (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Every call on a device shares the array: calls whose
+ * GPU work can overlap (other streams, other threads without ordering) race on it and
+ * must be serialised by the caller.  Synchronous on the graph's stream.
+ * Errors: INVALID_ARG (NULL, host out, vertex or window out of range, graph over the
+ * limits), TIMEOUT, CUDA. */
+kairos_status kairos_earliest_arrival_noalloc(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, uint32_t *out);
+
 /* ---- diagnostics -------------------------------------------------------------------- */
 
 const char *kairos_last_error(void);

@@ -110,6 +110,7 @@ SIGNATURES = {
     "kairos_last_kernel_ms": (ctypes.c_double, [_P]),
     "kairos_last_round_profile": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P]),
     "kairos_last_phase_cycles": (ctypes.c_int32, [_P, _P]),
+    "kairos_earliest_arrival_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, _P]),
 }
 
 
@@ -261,6 +262,14 @@ def kairos_earliest_arrival(g, n, src, ta, tw, out):
 def kairos_latest_departure(g, n, dst, ta, tw, out):
     _check_out(out, n)
     _check(lib().kairos_latest_departure(g, int(dst), int(ta), int(tw), _ptr(out)), "kairos_latest_departure")
+    return out
+
+
+def kairos_earliest_arrival_noalloc(g, n, src, ta, tw, out):
+    """Earliest arrival that allocates no device memory; out must be a CUDA tensor."""
+    _check_out(out, n)
+    _check(lib().kairos_earliest_arrival_noalloc(g, int(src), int(ta), int(tw), _ptr(out)),
+           "kairos_earliest_arrival_noalloc")
     return out
 
 
