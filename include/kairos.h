@@ -179,9 +179,13 @@ kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32
 /* ---- continuous-batching server ------------------------------------------------------ */
 
 typedef struct {
-    int32_t max_slots;      /* queries resident at once (lanes of the running batches); 0: 64 */
+    int32_t max_slots;      /* queries resident at once per query kind (lanes of the running
+                               edge-map): 2, 4, 8, 16 or 32; 0: 32.  Lowered at start while the
+                               device cannot hold that many beside reserve_bytes */
     int32_t queue_capacity; /* pending submissions before submit returns BUSY; 0: 4096 */
-    int64_t reserve_bytes;  /* device memory left free when admitting a slot; 0: 1 GiB */
+    int64_t reserve_bytes;  /* device memory to leave free; no query is admitted while free
+                               memory is below it; 0: 256 MiB */
+    int32_t rounds_per_slice; /* edge-map rounds per launch between admissions; 0: 4 */
 } kairos_serve_opts;
 
 typedef struct {
@@ -192,9 +196,14 @@ typedef struct {
     double latency_ms;        /* submit to completion, host clock */
 } kairos_result_info;
 
-/* Start a server thread on g (which must outlive it).  Queries submitted while others run
- * are admitted into free slots between edge-map rounds as slots and device memory allow.
- * Errors: INVALID_ARG, OOM, CUDA. */
+/* Start a server thread on g (which must outlive it).  It keeps one resumable batched
+ * edge-map per query kind (earliest arrival on the forward graph, latest departure on the
+ * mirrored one) and alternates launches of rounds_per_slice rounds between them.  Between
+ * launches it retires every lane whose query finished (no label changed in its last
+ * round: the labels are read out on the device into the ticket's buffer) and admits
+ * waiting queries into free lanes (their column is reset and their source joins the
+ * running frontier), so queries that arrive while others run share the device with them.
+ * Every answer equals that of the same query run alone.  Errors: INVALID_ARG, OOM, CUDA. */
 kairos_status kairos_serve_create(kairos_graph *g, const kairos_serve_opts *opts, kairos_server **out);
 
 /* Enqueue one query; out: uint32_t[n], host or device, must stay valid until the ticket

@@ -78,7 +78,8 @@ class kairos_graph_info(ctypes.Structure):
 
 
 class kairos_serve_opts(ctypes.Structure):
-    _fields_ = [("max_slots", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("reserve_bytes", ctypes.c_int64)]
+    _fields_ = [("max_slots", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("reserve_bytes", ctypes.c_int64),
+                ("rounds_per_slice", ctypes.c_int32)]
 
 
 class kairos_result_info(ctypes.Structure):
@@ -318,8 +319,8 @@ def kairos_autotune(g, sample) -> kairos_tuning:
     return best
 
 
-def kairos_serve_create(g, max_slots=0, queue_capacity=0, reserve_bytes=0):
-    opts = kairos_serve_opts(int(max_slots), int(queue_capacity), int(reserve_bytes))
+def kairos_serve_create(g, max_slots=0, queue_capacity=0, reserve_bytes=0, rounds_per_slice=0):
+    opts = kairos_serve_opts(int(max_slots), int(queue_capacity), int(reserve_bytes), int(rounds_per_slice))
     h = _P()
     _check(lib().kairos_serve_create(g, ctypes.byref(opts), ctypes.byref(h)), "kairos_serve_create")
     return h

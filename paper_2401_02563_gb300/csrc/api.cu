@@ -50,27 +50,6 @@ void Allocator::put(void *p) const {
     else cudaFree(p);
 }
 
-// Device checksum of rows: cs[i] = sum_v (v + 1) * x[i][v] mod 2^64, cnt[i] = #finite.
-__global__ void checksum_rows(const uint32_t *x, int64_t n, int rows, unsigned long long *cs, unsigned *cnt) {
-    for (int r = 0; r < rows; ++r) {
-        unsigned long long acc = 0;
-        unsigned c = 0;
-        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-            uint32_t y = x[(int64_t)r * n + v];
-            acc += (unsigned long long)(v + 1) * y;
-            c += (y != INF);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-            c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&cs[r], acc);
-            atomicAdd(&cnt[r], c);
-        }
-    }
-}
-
 }  // namespace kairos
 
 namespace {
@@ -211,6 +190,10 @@ kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, in
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;
     a.count_relaxed = count_relaxed;
+    a.resume = 0;
+    a.round_begin = 0;
+    a.round_end = 0xFFFFFFFFu;
+    a.running_mask = 0xFFFFFFFFu;
     static const int phase_clock = getenv("KAIROS_PHASE_CLOCK") ? atoi(getenv("KAIROS_PHASE_CLOCK")) : 0;
     a.phase_clock = phase_clock;
     int bps = 0;
@@ -294,31 +277,6 @@ kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_
                 }
             }
         }
-    }
-    return KAIROS_OK;
-}
-
-// Row checksums on the device (used by the server); x is a device pointer.
-kairos_status kairos_row_checksums(kairos_graph *g, const uint32_t *x, int rows, uint64_t *cs, uint32_t *reached) {
-    unsigned long long *d = (unsigned long long *)g->A.get((size_t)rows * 12 + 16);
-    if (!d) return fail(KAIROS_ERR_OOM, "checksum: device allocation failed");
-    unsigned *cnt = (unsigned *)(d + rows);
-    cudaStream_t s = g->stream;
-    cudaError_t e = cudaMemsetAsync(d, 0, (size_t)rows * 12, s);
-    if (e == cudaSuccess) {
-        checksum_rows<<<std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, 1024)), 256, 0, s>>>(x, g->n, rows, d, cnt);
-        e = cudaGetLastError();
-    }
-    std::vector<unsigned long long> hc(rows);
-    std::vector<unsigned> hn(rows);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), d, (size_t)rows * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hn.data(), cnt, (size_t)rows * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    g->A.put(d);
-    if (e != cudaSuccess) return cuda_fail(e, "checksum");
-    for (int r = 0; r < rows; ++r) {
-        cs[r] = hc[r];
-        reached[r] = hn[r];
     }
     return KAIROS_OK;
 }

@@ -80,6 +80,8 @@ struct EdgeMapCtr {
     PaddedU32 chunk_next[3]; // chunks claimed, by round mod 3
     PaddedU32 bnext[3];      // frontier batches claimed, by round mod 3
     PaddedU32 bdone[3];      // frontier batches finished, by round mod 3
+    PaddedU32 active[3];     // lanes that lowered some label, by round mod 3
+    unsigned int last_active;  // `active` of the last completed round
     unsigned long long scanned;
     unsigned long long relaxed[MAX_LANES];
     unsigned int reached[MAX_LANES];
@@ -141,8 +143,24 @@ struct EdgeMapArgs {
     uint32_t max_rounds;
     int warp_max_edges, chunk_edges, dense_div;
     int count_relaxed;     // nonzero: count relaxations per lane (query statistics)
+    // resumable operation: resume != 0 keeps the state of an earlier launch (no init, no
+    // seeding, no readout) and runs rounds [round_begin, round_end); lanes outside
+    // running_mask take no part
+    int resume;
+    uint32_t round_begin, round_end;
+    uint32_t running_mask;
     int phase_clock;       // nonzero: accumulate per-phase cycle counts (diagnostics)
 };
+
+// Between resumable launches (serving): column operations on the [n][W] state.
+// Read lane q's labels into out (mirrored back when mirror), adding the reached count and
+// sum of (v + 1) * label to stats[0..1].
+cudaError_t column_readout(const uint32_t *arr, int64_t n, int W, int q, int mirror, uint32_t *out,
+                           unsigned long long *stats, cudaStream_t s);
+// Reset the lanes in mask to the unreached state (labels and scan bounds).
+cudaError_t column_reset(uint32_t *arr, uint32_t *prev, int64_t n, int W, uint32_t mask, cudaStream_t s);
+// Seed lane q at source src with label ta into the frontier of round r (bitmap + queue).
+cudaError_t seed_lane(const EdgeMapArgs &a, int W, int q, int32_t src, uint32_t ta, uint32_t r, cudaStream_t s);
 
 // Launch one persistent edge-map (cooperative: every block resident).
 cudaError_t edgemap_launch(const EdgeMapArgs &a, int lanes, int lam_bits, int grid, cudaStream_t s);

@@ -28,6 +28,8 @@
 // round.  Large frontiers are swept from the bitmap in vertex order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace kairos {
@@ -284,7 +286,7 @@ __device__ __forceinline__ void frontier_append_k(uint32_t needmask, const int32
 template <int W, typename ActF, typename BoundsF>
 __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)[K_EDGES], const uint32_t (&tt)[K_EDGES],
                                         const uint32_t (&ll)[K_EDGES], ActF actf, BoundsF bounds, BlockSmem &B,
-                                        unsigned long long &cnt1, int lane, int nxt, int n3) {
+                                        unsigned long long &cnt1, int lane, int nxt, int n3, uint32_t &hit) {
     uint32_t mark = 0;  // bit k: edge k lowered its head in some lane
     if constexpr (W == 1) {
         bool ok[K_EDGES];
@@ -304,6 +306,7 @@ __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)
             if (ok[k] && tau < cur[k]) {
                 atomicMin(a.arr + d[k], tau);  // result unused: a reduction
                 mark |= 1u << k;
+                hit = 1u;
             }
         }
     } else {
@@ -355,6 +358,7 @@ __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)
                     if (((cand >> q) & 1u) && tau < cur[q]) {
                         atomicMin(row + q, tau);  // result unused: a reduction
                         mark |= 1u << k;
+                        hit |= 1u << q;
                     }
             }
         }
@@ -375,7 +379,7 @@ __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)
 template <int W, typename LamT>
 __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, BlockSmem &B, const LaneReg &R, int lane,
                                        int32_t u, int nxt, int c3, int n3, unsigned long long &cnt1,
-                                       unsigned long long &scanned, PhaseClock &pc) {
+                                       unsigned long long &scanned, PhaseClock &pc, uint32_t &hit) {
     const LamT *__restrict__ lam = (const LamT *)a.lam;
     // 1. lane states of the 32 slots: thread (k, lane) handles slot (32k + lane) / W, lane q
 #pragma unroll
@@ -504,7 +508,7 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, Blo
                        th = S.thr[sl[k]][q];
                        li = S.lim[sl[k]][q];
                    },
-                   B, cnt1, lane, nxt, n3);
+                   B, cnt1, lane, nxt, n3, hit);
     }
     __syncwarp();
     pc.mark(3);
@@ -526,7 +530,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
     LaneReg R;
     R.q = lane % W;
     R.grp = lane / W;
-    R.on = R.q < a.lanes.nlanes;
+    R.on = R.q < a.lanes.nlanes && ((a.running_mask >> R.q) & 1u);
     R.tw = a.lanes.tw[R.q];
     R.lim_cap = R.tw + 1u;
     R.strict = (a.lanes.strict_mask >> R.q) & 1u;
@@ -541,6 +545,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
     pc.init(a.phase_clock != 0);
 
     // ---- initial labels (Alg. 2: t[x] = window start, t[v] = infinity) ----
+    if (!a.resume) {
     for (size_t i = tid; i < (size_t)n * W; i += nthr) {
         a.arr[i] = INF;
         a.prev[i] = INF;
@@ -550,7 +555,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
         a.bm[1][i] = 0u;
     }
     if (!grid_sync(C, &B.flag)) return;
-    if (blockIdx.x == 0 && threadIdx.x < (unsigned)a.lanes.nlanes) {
+    if (blockIdx.x == 0 && threadIdx.x < (unsigned)a.lanes.nlanes && ((a.running_mask >> threadIdx.x) & 1u)) {
         const int qq = threadIdx.x;
         const int32_t s = a.lanes.src[qq];
         a.arr[(size_t)s * W + qq] = a.lanes.ta[qq];
@@ -559,10 +564,12 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
         if (!(old & bit)) a.queue[0][atomicAdd(&C->qcount[0].v, 1u)] = s;
     }
     if (!grid_sync(C, &B.flag)) return;
+    }
 
     // ---- rounds ----
-    unsigned r = 0;
-    for (;; ++r) {
+    unsigned r = a.round_begin;
+    for (; r < a.round_end; ++r) {
+        uint32_t hit = 0;  // lanes this thread lowered a label in, this round
         const int cur = r & 1, nxt = cur ^ 1;
         const int c3 = r % 3, n3 = (r + 1) % 3, p3 = (r + 2) % 3;
         const unsigned F = __ldcg(&C->qcount[c3].v);
@@ -583,6 +590,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
             C->chunk_next[n3].v = 0;
             C->bnext[n3].v = 0;
             C->bdone[n3].v = 0;
+            C->active[n3].v = 0;
         }
         const bool dense = a.dense_div > 0 && (int64_t)F * a.dense_div > n;
         // work of the round: batches of 32 queued vertices (or 1024-vertex bitmap stripes),
@@ -597,7 +605,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                     const unsigned i = b * 32 + lane;
                     const int32_t u = (i < F) ? __ldcg(&a.queue[cur][i]) : -1;
                     if (u >= 0) atomicAnd(&a.bm[cur][u >> 5], ~(1u << (u & 31)));
-                    expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned, pc);
+                    expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned, pc, hit);
                 } else {
                     // ballot-compact the 1024-vertex stripe, 32 vertices at a time
                     const size_t wb = (size_t)b * 32;
@@ -620,7 +628,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                         const uint32_t pj = __shfl_sync(FULL, pre, j);
                         int32_t u = -1;
                         if (k < total) u = (int32_t)((wb + j) * 32 + __fns(bj, 0, (int)(k - pj) + 1));
-                        expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned, pc);
+                        expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned, pc, hit);
                     }
                 }
                 __syncwarp();
@@ -735,18 +743,22 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                                    li = INF;
                                }
                            },
-                           B, cnt1, lane, nxt, n3);
+                           B, cnt1, lane, nxt, n3, hit);
             }
             __syncwarp();
             pc.mark(5);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hit |= __shfl_xor_sync(FULL, hit, o);
+        if (lane == 0 && hit) atomicOr(&C->active[c3].v, hit);
         pc.mark(7);
         if (!grid_sync(C, &B.flag)) return;
         pc.mark(6);
+        if (tid == 0) C->last_active = __ldcg(&C->active[c3].v);
     }
 
     // ---- read out: out[row_q][v] = label (mirrored back for latest departure) ----
-    for (size_t i = tid; i < (size_t)n * W; i += nthr) {
+    for (size_t i = tid; !a.resume && i < (size_t)n * W; i += nthr) {
         // nthr is a multiple of W, so this thread always sees lane R.q
         if (!R.on) continue;
         const size_t v = i / W;
@@ -773,7 +785,8 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
         if (lane == 0) atomicAdd(&C->relaxed[0], cnt1);
     } else {
         __syncthreads();
-        if (threadIdx.x < (unsigned)a.lanes.nlanes) atomicAdd(&C->relaxed[threadIdx.x], (unsigned long long)B.cnt[threadIdx.x]);
+        if (threadIdx.x < (unsigned)W && B.cnt[threadIdx.x])
+            atomicAdd(&C->relaxed[threadIdx.x], (unsigned long long)B.cnt[threadIdx.x]);
     }
     if (tid == 0) C->rounds = r;
     pc.mark(7);
@@ -834,7 +847,65 @@ int max_blocks_l(int lanes) {
     }
 }
 
+__global__ void column_readout_kernel(const uint32_t *arr, int64_t n, int W, int q, int mirror, uint32_t *out,
+                                      unsigned long long *stats) {
+    unsigned long long cnt = 0, cs = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = arr[v * W + q];
+        const uint32_t y = (mirror && x != INF) ? TMAX - x : x;
+        out[v] = y;
+        cnt += (x != INF);
+        cs += (unsigned long long)(v + 1) * y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_xor_sync(FULL, cnt, o);
+        cs += __shfl_xor_sync(FULL, cs, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&stats[0], cnt);
+        atomicAdd(&stats[1], cs);
+    }
+}
+
+__global__ void column_reset_kernel(uint32_t *arr, uint32_t *prev, int64_t n, int W, uint32_t mask) {
+    const int64_t total = n * W;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        if ((mask >> (int)(i % W)) & 1u) {
+            arr[i] = INF;
+            prev[i] = INF;
+        }
+    }
+}
+
+// Lane q's source enters the frontier of round r: its label, then the bitmap bit and a
+// queue slot unless the vertex is already queued for that round.
+__global__ void seed_lane_kernel(uint32_t *arr, uint32_t *bm, int32_t *queue, unsigned *count, int W, int q,
+                                 int32_t src, uint32_t ta) {
+    arr[(size_t)src * W + q] = ta;
+    const uint32_t bit = 1u << (src & 31);
+    if (!(atomicOr(&bm[src >> 5], bit) & bit)) queue[atomicAdd(count, 1u)] = src;
+}
+
 }  // namespace
+
+cudaError_t column_readout(const uint32_t *arr, int64_t n, int W, int q, int mirror, uint32_t *out,
+                           unsigned long long *stats, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 2048);
+    column_readout_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(arr, n, W, q, mirror, out, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t column_reset(uint32_t *arr, uint32_t *prev, int64_t n, int W, uint32_t mask, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>((n * W + 255) / 256, 8192);
+    column_reset_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(arr, prev, n, W, mask);
+    return cudaGetLastError();
+}
+
+cudaError_t seed_lane(const EdgeMapArgs &a, int W, int q, int32_t src, uint32_t ta, uint32_t r, cudaStream_t s) {
+    seed_lane_kernel<<<1, 1, 0, s>>>(a.arr, a.bm[r & 1], a.queue[r & 1], &a.ctr->qcount[r % 3].v, W, q, src, ta);
+    return cudaGetLastError();
+}
 
 size_t edgemap_smem_bytes(int lanes) {
     switch (lanes) {
