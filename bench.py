@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--no-single", action="store_true", help="skip the one-query-per-launch comparison")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-rates", default="1000,4000,16000")
+    p.add_argument("--serve-queries", type=int, default=400)
     return p.parse_args()
 
 
@@ -132,6 +135,90 @@ def union_admissible(torch, E, queries, group, labels_dev):
             adm = (lv != INF) & (E["tau"] <= lim) & (E["t"] >= q.ta)
         anyadm |= adm
     return int(anyadm.sum().item())
+
+
+def serve_stream(el, span, count, seed):
+    """Served query mix: 70% earliest arrival / 30% latest departure, uniform vertices
+    (with an out- / in-edge), window length log-uniform from 2^10 to the whole span."""
+    kinds = [synth.EA if synth.u01(synth.draw(seed, q, 220)) < 0.7 else synth.LD for q in range(count)]
+    v_ea = synth.pick_vertices(el, count, seed, True, False)
+    v_ld = synth.pick_vertices(el, count, seed ^ 0x1D, False, True)
+    wins = synth.log_uniform_windows(count, seed, span, 10.0, math.log2(span))
+    return [synth.Query(k, v_ea[q] if k == synth.EA else v_ld[q], ta, tw)
+            for q, (k, (ta, tw)) in enumerate(zip(kinds, wins))]
+
+
+def measure_serving(torch, kx, g, el, span, rates, per_rate, slots):
+    """Open-loop Poisson arrivals at each rate through kairos_serve_submit/poll; latency is
+    the server's submit-to-completion time.  The same stream is also answered one query
+    per launch (kairos_earliest_arrival / kairos_latest_departure, FIFO) for comparison."""
+    import threading
+    n = el.n
+    pool = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(256)]
+    res = {"slots_per_kind": slots, "queries_per_rate": per_rate, "rates": []}
+    server = kx.kairos_serve_create(g.handle, max_slots=slots)
+    try:
+        for ri, rate in enumerate(rates):
+            qs = serve_stream(el, span, per_rate, 0x5E7E + ri)
+            arrive = synth.poisson_arrivals(per_rate, rate, 0xA77 + ri)
+            lat = [None] * per_rate
+            tickets = [None] * per_rate
+            free = list(range(len(pool)))
+            lock = threading.Condition()
+            done_at = [0.0]
+
+            def poller():
+                for i in range(per_rate):
+                    with lock:
+                        while tickets[i] is None:
+                            lock.wait()
+                        t, buf = tickets[i]
+                    info = kx.kairos_serve_poll(server, t, -1)
+                    lat[i] = info.latency_ms
+                    with lock:
+                        free.append(buf)
+                        lock.notify_all()
+                done_at[0] = time.perf_counter()
+
+            th = threading.Thread(target=poller)
+            th.start()
+            t0 = time.perf_counter()
+            for i, q in enumerate(qs):
+                while time.perf_counter() - t0 < arrive[i]:
+                    pass
+                with lock:
+                    while not free:
+                        lock.wait()
+                    buf = free.pop()
+                t = kx.kairos_serve_submit(server, q, pool[buf])
+                with lock:
+                    tickets[i] = (t, buf)
+                    lock.notify_all()
+            th.join()
+            wall = done_at[0] - t0
+            lat_arr = np.array(lat)
+            res["rates"].append({"offered_qps": rate, "served_qps": per_rate / wall,
+                                 "p50_ms": float(np.percentile(lat_arr, 50)),
+                                 "p99_ms": float(np.percentile(lat_arr, 99))})
+    finally:
+        kx.kairos_serve_destroy(server)
+    # one query per launch, FIFO, on the last stream: service time per query and the
+    # queueing latency the same arrivals would see
+    row = pool[0]
+    t_serv = []
+    for q in qs:
+        t1 = time.perf_counter()
+        (g.earliest_arrival if q.kind == 0 else g.latest_departure)(q.vertex, q.ta, q.tw, row)
+        t_serv.append(time.perf_counter() - t1)
+    finish, lat1 = 0.0, []
+    for a_i, s_i in zip(arrive, t_serv):
+        start = max(a_i, finish)
+        finish = start + s_i
+        lat1.append((finish - a_i) * 1e3)
+    res["one_query_per_launch"] = {"qps_capacity": len(qs) / sum(t_serv),
+                                   "p50_ms_at_last_rate": float(np.percentile(lat1, 50)),
+                                   "p99_ms_at_last_rate": float(np.percentile(lat1, 99))}
+    return res
 
 
 def cpu_baseline(el, queries, budget_s=20.0):
@@ -317,6 +404,10 @@ def main():
             e2e_s = (time.perf_counter() - t0) / args.steps
             e2e = {"value": world * te_step / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 16,
                    "d2h_bytes_per_step": Q * n * 4, "note": "queries in, every label row copied to pageable host memory"}
+        served = None
+        if not args.no_serve:
+            rates = [float(x) for x in args.serve_rates.split(",") if x]
+            served = measure_serving(torch, kx, g, el, w.graph.t_span, rates, args.serve_queries, 32)
         g.close()
 
     if rank != 0:
@@ -341,6 +432,7 @@ def main():
                      "traffic": None, "peak_kind": peak_kind, "kernel": "edgemap_kernel",
                      "launches_per_step": n_launch, "avg_launch_ms": launch_ms,
                      "algorithmic_bytes_per_step": bytes_step},
+        "served": served,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * n_launch,

@@ -186,6 +186,11 @@ kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, in
     a.out_is_arr = (arr_alias != nullptr && out == arr_alias) ? 1 : 0;
     a.lanes = lp;
     a.max_rounds = (uint32_t)std::min<int64_t>(n + 1, 0xFFFFFFF0LL);
+    a.spin_limit = DEFAULT_SPIN_LIMIT;
+    // test hooks: shrink the device wait limit or the round cap to exercise the TIMEOUT
+    // paths without a fault or a hang (read per launch)
+    if (const char *v = getenv("KAIROS_SPIN_LIMIT")) a.spin_limit = strtoull(v, nullptr, 10);
+    if (const char *v = getenv("KAIROS_ROUND_CAP")) a.max_rounds = (uint32_t)strtoul(v, nullptr, 10);
     a.warp_max_edges = g->tuning.warp_max_edges;
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;

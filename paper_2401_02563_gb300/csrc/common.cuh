@@ -21,6 +21,7 @@ constexpr int FENCE_B = 1 << FENCE_SHIFT;
 constexpr int EM_THREADS = 256;         // edge-map block size
 constexpr int MAX_LANES = 32;
 constexpr int PROFILE_ROUNDS = 256;
+constexpr unsigned long long DEFAULT_SPIN_LIMIT = 1ull << 24;  // with backoff sleeps: seconds
 
 // Device-side error codes reported through EdgeMapCtr::err.
 enum : int { KERR_NONE = 0, KERR_BARRIER_TIMEOUT = 1, KERR_ROUNDS = 2, KERR_CAPACITY = 3, KERR_WAIT_TIMEOUT = 4 };
@@ -150,6 +151,7 @@ struct EdgeMapArgs {
     uint32_t round_begin, round_end;
     uint32_t running_mask;
     int phase_clock;       // nonzero: accumulate per-phase cycle counts (diagnostics)
+    unsigned long long spin_limit;  // polls before a device wait gives up (KERR_*_TIMEOUT)
 };
 
 // Between resumable launches (serving): column operations on the [n][W] state.

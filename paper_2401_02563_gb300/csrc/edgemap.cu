@@ -36,9 +36,7 @@ namespace kairos {
 namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr unsigned long long BARRIER_SPIN_LIMIT = 1ull << 24;  // with 128 ns sleeps: > 2 s
 
-constexpr unsigned long long WAIT_SPIN_LIMIT = 1ull << 24;     // chunk publication waits
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
@@ -59,7 +57,7 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
 // Grid-wide barrier of a cooperative launch (all blocks resident).  Every wait is bounded:
 // past the limit the block records KERR_BARRIER_TIMEOUT and leaves.  Returns true when the
 // launch may go on (no error recorded anywhere).
-__device__ __forceinline__ bool grid_sync(EdgeMapCtr *c, int *s_flag) {
+__device__ __forceinline__ bool grid_sync(EdgeMapCtr *c, int *s_flag, unsigned long long limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned gen = ld_acquire(&c->bar_gen);
@@ -72,7 +70,7 @@ __device__ __forceinline__ bool grid_sync(EdgeMapCtr *c, int *s_flag) {
         } else {
             unsigned long long spins = 0;
             while (ld_acquire(&c->bar_gen) == gen) {
-                if (++spins > BARRIER_SPIN_LIMIT) {
+                if (++spins > limit) {
                     atomicCAS(&c->err, 0, KERR_BARRIER_TIMEOUT);
                     break;
                 }
@@ -554,7 +552,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
         a.bm[0][i] = 0u;
         a.bm[1][i] = 0u;
     }
-    if (!grid_sync(C, &B.flag)) return;
+    if (!grid_sync(C, &B.flag, a.spin_limit)) return;
     if (blockIdx.x == 0 && threadIdx.x < (unsigned)a.lanes.nlanes && ((a.running_mask >> threadIdx.x) & 1u)) {
         const int qq = threadIdx.x;
         const int32_t s = a.lanes.src[qq];
@@ -563,7 +561,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
         const uint32_t old = atomicOr(&a.bm[0][s >> 5], bit);
         if (!(old & bit)) a.queue[0][atomicAdd(&C->qcount[0].v, 1u)] = s;
     }
-    if (!grid_sync(C, &B.flag)) return;
+    if (!grid_sync(C, &B.flag, a.spin_limit)) return;
     }
 
     // ---- rounds ----
@@ -653,8 +651,8 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                         state = 2;
                         break;
                     }
-                    if (__ldcg(&C->err) != 0 || ++spins > WAIT_SPIN_LIMIT) {
-                        if (spins > WAIT_SPIN_LIMIT) atomicCAS(&C->err, 0, KERR_WAIT_TIMEOUT);
+                    if (__ldcg(&C->err) != 0 || ++spins > a.spin_limit) {
+                        if (spins > a.spin_limit) atomicCAS(&C->err, 0, KERR_WAIT_TIMEOUT);
                         state = 2;
                         break;
                     }
@@ -677,7 +675,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
                         state = 2;
                         break;
                     }
-                    if (++spins > WAIT_SPIN_LIMIT) {
+                    if (++spins > a.spin_limit) {
                         atomicCAS(&C->err, 0, KERR_WAIT_TIMEOUT);
                         state = 2;
                         break;
@@ -752,7 +750,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
         for (int o = 16; o > 0; o >>= 1) hit |= __shfl_xor_sync(FULL, hit, o);
         if (lane == 0 && hit) atomicOr(&C->active[c3].v, hit);
         pc.mark(7);
-        if (!grid_sync(C, &B.flag)) return;
+        if (!grid_sync(C, &B.flag, a.spin_limit)) return;
         pc.mark(6);
         if (tid == 0) C->last_active = __ldcg(&C->active[c3].v);
     }

@@ -157,6 +157,7 @@ extern "C" kairos_status kairos_earliest_arrival_noalloc(kairos_graph *g, int32_
     a.dense_div = g->tuning.dense_div;
     a.round_end = 0xFFFFFFFFu;
     a.running_mask = 0xFFFFFFFFu;
+    a.spin_limit = DEFAULT_SPIN_LIMIT;
     int bps = 0;
     int grid = edgemap_max_grid(1, g->lam_bits, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "no-allocation query: no resident launch shape");

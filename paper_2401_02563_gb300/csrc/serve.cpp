@@ -167,6 +167,7 @@ EdgeMapArgs session_args(kairos_graph *g, Session &S) {
     a.lanes = S.lp;
     a.lanes.nlanes = S.W;
     a.max_rounds = 0xFFFFFFFFu;
+    a.spin_limit = DEFAULT_SPIN_LIMIT;
     a.warp_max_edges = g->tuning.warp_max_edges;
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;

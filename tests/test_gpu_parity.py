@@ -282,3 +282,28 @@ def test_medium_full_size_sampled_against_oracle(medium):
     for i, q in enumerate(qs[:64]):
         assert oracle.certify_ea(el, q.vertex, q.ta, q.tw, q.strict, got[i]) == (0, 0), q
     g.set_tuning(lanes=1)
+
+
+# ---- failure paths: device waits and the round cap give up with a status ----------------------
+
+def test_device_wait_and_round_cap_return_timeout(tiny, monkeypatch):
+    """A wait limit of zero polls makes every grid-barrier wait run out (nothing can satisfy
+    it in time): the call must return KAIROS_ERR_TIMEOUT, not hang or fault, and the
+    context must stay usable.  Likewise a round cap below the rounds a query needs."""
+    el, orc, g = tiny
+    g.index(64)
+    g.set_tuning(lanes=1)
+    q = synth.workload_queries(1, el)[0]
+    out = dev_out(el.n)
+    monkeypatch.setenv("KAIROS_SPIN_LIMIT", "0")
+    with pytest.raises(kx.KairosError) as e:
+        g.earliest_arrival(q.vertex, q.ta, q.tw, out)
+    assert e.value.status == kx.KAIROS_ERR_TIMEOUT
+    monkeypatch.delenv("KAIROS_SPIN_LIMIT")
+    monkeypatch.setenv("KAIROS_ROUND_CAP", "1")
+    with pytest.raises(kx.KairosError) as e:
+        g.earliest_arrival(q.vertex, q.ta, q.tw, out)
+    assert e.value.status == kx.KAIROS_ERR_TIMEOUT
+    monkeypatch.delenv("KAIROS_ROUND_CAP")
+    g.earliest_arrival(q.vertex, q.ta, q.tw, out)
+    assert np.array_equal(labels(out), orc.query(q))
