@@ -221,6 +221,20 @@ def measure_serving(torch, kx, g, el, span, rates, per_rate, slots):
     return res
 
 
+def replica_reduce(step_ms, te_step, world, device):
+    """Across replicas: the slowest rank's step time and the total traversed edges.  Replicas
+    hold the whole graph and answer their own query shard, so this is the only exchange."""
+    if world <= 1:
+        return step_ms, te_step
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    e = torch.tensor([te_step], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(e.item())
+
+
 def cpu_baseline(el, queries, budget_s=20.0):
     """The oracle as it stands, single-threaded on a host core, on a bounded sample."""
     import oracle
@@ -307,7 +321,7 @@ def main():
 
     w = synth.WORKLOADS[args.workload]
     el = synth.rmat(w.graph)
-    queries = synth.workload_queries(args.workload, el)
+    queries = synth.workload_queries(args.workload, el, shard=rank)
     Q, n, m = len(queries), el.n, el.m
     stream = torch.cuda.Stream()
     R = 10 if el.lam.dtype == np.uint16 else 12
@@ -349,13 +363,11 @@ def main():
         step_ms = ev0.elapsed_time(ev1) / args.steps
         te_step = sum(s.relaxed_edges for s in stats)  # identical every step: exact integer counts
         scanned_step = sum(s.scanned_edges for s in stats) // lanes  # one count per launch
+        step_ms, te_all = replica_reduce(step_ms, te_step, world, "cuda")
         if dist:
-            t = torch.tensor([step_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            step_ms = float(t.item())
             dist.barrier()
         clocks = clk.summary()
-        value = world * te_step / (step_ms / 1e3) / 1e9
+        value = te_all / (step_ms / 1e3) / 1e9
         groups = launch_groups(queries, lanes)
         n_launch = len(groups)
 
@@ -402,8 +414,9 @@ def main():
             for _ in range(args.steps):
                 g.batch(queries, host)
             e2e_s = (time.perf_counter() - t0) / args.steps
-            e2e = {"value": world * te_step / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 16,
+            e2e = {"value": te_all / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 16,
                    "d2h_bytes_per_step": Q * n * 4, "note": "queries in, every label row copied to pageable host memory"}
+        graph_launches = g.info().graph_launches
         served = None
         if not args.no_serve:
             rates = [float(x) for x in args.serve_rates.split(",") if x]
@@ -425,7 +438,7 @@ def main():
                    "l2": "inputs larger than L2 (graph 2 x 0.4 GB)"},
         "queries_per_s": world * Q / (step_ms / 1e3),
         "relaxed_edges_per_step": te_step, "scanned_edges_per_step": scanned_step,
-        "build_ms": info.build_ms, "index_ms": info.index_ms,
+        "build_ms": info.build_ms, "index_ms": info.index_ms, "graph_launches": graph_launches,
         "single_launch": single,
         "batched_vs_single_qps": (Q / (step_ms / 1e3)) / single["queries_per_s"] if single else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

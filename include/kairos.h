@@ -124,6 +124,7 @@ typedef struct {
     int64_t device_bytes;        /* graph + index + query workspace currently held */
     double build_ms;             /* last kairos_graph_build, device time */
     double index_ms;             /* last kairos_index_build, device time */
+    int64_t graph_launches;      /* query calls run as a captured CUDA graph (capture or replay) */
 } kairos_graph_info;
 
 /* ---- graph and index -------------------------------------------------------------- */

@@ -74,7 +74,8 @@ class kairos_tuning(ctypes.Structure):
 class kairos_graph_info(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_int64), ("n_edges", ctypes.c_int64), ("lambda_bits", ctypes.c_int32),
                 ("index_threshold", ctypes.c_uint32), ("indexed_vertices", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double), ("index_ms", ctypes.c_double)]
+                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double), ("index_ms", ctypes.c_double),
+                ("graph_launches", ctypes.c_int64)]
 
 
 class kairos_serve_opts(ctypes.Structure):

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <string>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -156,8 +157,8 @@ void lane_set(LaneParams &lp, int q, const kairos_query &Q, int64_t row) {
     lp.row[q] = row;
 }
 
-kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, int lanes, uint32_t *out,
-                         int64_t stride, uint32_t *arr_alias, int count_relaxed, EdgeMapCtr *res) {
+EdgeMapArgs make_args(kairos_graph *g, const Csr &c, const LaneParams &lp, uint32_t *out, int64_t stride,
+                      uint32_t *arr_alias, int count_relaxed, EdgeMapCtr *ctr) {
     auto &w = g->work;
     const int64_t n = g->n, nwords = (n + 31) / 32;
     EdgeMapArgs a;
@@ -180,7 +181,7 @@ kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, in
     a.chunk_owner = w.chunk_owner;
     a.cap_big = w.cap_big;
     a.cap_chunks = w.cap_chunks;
-    a.ctr = w.ctr;
+    a.ctr = ctr;
     a.out = out;
     a.out_stride = stride;
     a.out_is_arr = (arr_alias != nullptr && out == arr_alias) ? 1 : 0;
@@ -188,7 +189,7 @@ kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, in
     a.max_rounds = (uint32_t)std::min<int64_t>(n + 1, 0xFFFFFFF0LL);
     a.spin_limit = DEFAULT_SPIN_LIMIT;
     // test hooks: shrink the device wait limit or the round cap to exercise the TIMEOUT
-    // paths without a fault or a hang (read per launch)
+    // paths without a fault or a hang (read per call)
     if (const char *v = getenv("KAIROS_SPIN_LIMIT")) a.spin_limit = strtoull(v, nullptr, 10);
     if (const char *v = getenv("KAIROS_ROUND_CAP")) a.max_rounds = (uint32_t)strtoul(v, nullptr, 10);
     a.warp_max_edges = g->tuning.warp_max_edges;
@@ -201,32 +202,54 @@ kairos_status run_launch(kairos_graph *g, const Csr &c, const LaneParams &lp, in
     a.running_mask = 0xFFFFFFFFu;
     static const int phase_clock = getenv("KAIROS_PHASE_CLOCK") ? atoi(getenv("KAIROS_PHASE_CLOCK")) : 0;
     a.phase_clock = phase_clock;
-    int bps = 0;
-    int grid = edgemap_max_grid(lanes, g->lam_bits, &bps);
-    if (grid <= 0) return fail(KAIROS_ERR_CUDA, "edge-map: no resident launch shape (occupancy query failed)");
-    if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
-    cudaStream_t s = g->stream;
-    KAIROS_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(EdgeMapCtr), s), "edge-map counters");
-    KAIROS_CUDA(cudaEventRecord(w.ev0, s), "event record");
-    KAIROS_CUDA(edgemap_launch(a, lanes, g->lam_bits, grid, s), "edge-map launch");
-    KAIROS_CUDA(cudaEventRecord(w.ev1, s), "event record");
-    KAIROS_CUDA(cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(EdgeMapCtr), cudaMemcpyDeviceToHost, s), "edge-map counters");
-    KAIROS_CUDA(cudaStreamSynchronize(s), "edge-map");
-    float ms = 0;
-    KAIROS_CUDA(cudaEventElapsedTime(&ms, w.ev0, w.ev1), "event time");
-    g->last_kernel_ms += ms;
-    *res = *w.ctr_host;
-    if (res->err == KERR_BARRIER_TIMEOUT) return fail(KAIROS_ERR_TIMEOUT, "edge-map: a grid barrier wait ran past its limit");
-    if (res->err == KERR_WAIT_TIMEOUT) return fail(KAIROS_ERR_TIMEOUT, "edge-map: a wait for a published chunk ran past its limit");
-    if (res->err == KERR_ROUNDS) return fail(KAIROS_ERR_TIMEOUT, "edge-map: round cap (n + 1) reached");
-    if (res->err) return fail(KAIROS_ERR_INTERNAL, "edge-map: split-range capacity exceeded");
+    return a;
+}
+
+kairos_status ctr_error(int err) {
+    if (err == KERR_BARRIER_TIMEOUT) return fail(KAIROS_ERR_TIMEOUT, "edge-map: a grid barrier wait ran past its limit");
+    if (err == KERR_WAIT_TIMEOUT) return fail(KAIROS_ERR_TIMEOUT, "edge-map: a wait for a published chunk ran past its limit");
+    if (err == KERR_ROUNDS) return fail(KAIROS_ERR_TIMEOUT, "edge-map: round cap (n + 1) reached");
+    return fail(KAIROS_ERR_INTERNAL, "edge-map: split-range capacity exceeded");
+}
+
+// One launch of a call: its arguments and the queries of its lanes.
+struct Planned {
+    EdgeMapArgs a;
+    std::vector<int> qid;
+    const uint32_t *host_src;  // device rows to copy to host outputs (nullptr: none)
+};
+
+kairos_status ensure_ctr_slots(kairos_graph *g, size_t count) {
+    auto &w = g->work;
+    if (w.ctr_slots >= count) return KAIROS_OK;
+    g->A.put(w.ctrs);
+    if (w.ctrs_host) cudaFreeHost(w.ctrs_host);
+    w.ctrs = nullptr;
+    w.ctrs_host = nullptr;
+    w.ctr_slots = 0;
+    const size_t want = std::max<size_t>(count, 8);
+    w.ctrs = (EdgeMapCtr *)g->A.get(want * sizeof(EdgeMapCtr));
+    if (!w.ctrs) return fail(KAIROS_ERR_OOM, "query counters: device allocation failed");
+    KAIROS_CUDA(cudaMallocHost(&w.ctrs_host, want * sizeof(EdgeMapCtr)), "query counters: pinned allocation");
+    w.ctr_slots = want;
     return KAIROS_OK;
+}
+
+void drop_graph(kairos_graph *g) {
+    auto &w = g->work;
+    if (w.graph_exec) cudaGraphExecDestroy(w.graph_exec);
+    w.graph_exec = nullptr;
+    w.graph_key.clear();
+    cudaGetLastError();
 }
 
 }  // namespace
 
 // Shared by the public query calls, the autotuner and the server.  out == nullptr runs the
-// queries without writing labels anywhere (timing only).
+// queries without writing labels anywhere (timing only).  All launches of the call are
+// enqueued back to back (one counter slot each) and read back once; when the outputs are
+// device memory and the graph has its own stream, the whole sequence is captured into a
+// CUDA graph, which is replayed while the same call repeats.
 kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_t nq, uint32_t *out,
                                  kairos_query_stats *stats, int lanes) {
     const int64_t n = g->n;
@@ -236,6 +259,9 @@ kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_
     auto &w = g->work;
     g->last_kernel_ms = 0;
     cudaStream_t s = g->stream;
+
+    // plan the launches: queries grouped by kind, `lanes` per launch
+    std::vector<Planned> plan;
     std::vector<int> idx;
     for (int kind = 0; kind < 2; ++kind) {
         idx.clear();
@@ -249,37 +275,103 @@ kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_
             lp.nlanes = k;
             uint32_t *o = nullptr, *alias = nullptr;
             for (int j = 0; j < k; ++j) lane_set(lp, j, qs[idx[c + j]], j);
+            const uint32_t *host_src = nullptr;
             if (lanes == 1) {
                 alias = (out && dev) ? out + (int64_t)idx[c] * n : w.arr;
                 o = out ? alias : nullptr;
+                if (out && !dev) host_src = w.arr;
             } else if (out) {
                 if (dev) {
                     o = out;
                     for (int j = 0; j < k; ++j) lp.row[j] = idx[c + j];
                 } else {
                     o = w.stage;
+                    host_src = w.stage;
                 }
             }
-            EdgeMapCtr res;
-            st = run_launch(g, csr, lp, lanes, o, n, alias, stats != nullptr, &res);
-            if (st != KAIROS_OK) return st;
-            if (out && !dev) {
-                for (int j = 0; j < k; ++j) {
-                    const uint32_t *srcrow = lanes == 1 ? w.arr : w.stage + (int64_t)j * n;
-                    KAIROS_CUDA(cudaMemcpyAsync(out + (int64_t)idx[c + j] * n, srcrow, (size_t)n * 4,
-                                                cudaMemcpyDeviceToHost, s),
+            Planned P;
+            P.a = make_args(g, csr, lp, o, n, alias, stats != nullptr, nullptr);
+            P.qid.assign(idx.begin() + c, idx.begin() + c + k);
+            P.host_src = host_src;
+            plan.push_back(std::move(P));
+        }
+    }
+    if (plan.empty()) return KAIROS_OK;
+    st = ensure_ctr_slots(g, plan.size());
+    if (st != KAIROS_OK) return st;
+    for (size_t i = 0; i < plan.size(); ++i) plan[i].a.ctr = w.ctrs + i;
+    int bps = 0;
+    int grid = edgemap_max_grid(lanes, g->lam_bits, &bps);
+    if (grid <= 0) return fail(KAIROS_ERR_CUDA, "edge-map: no resident launch shape (occupancy query failed)");
+    if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
+
+    auto enqueue = [&](bool direct) -> kairos_status {
+        for (size_t i = 0; i < plan.size(); ++i) {
+            KAIROS_CUDA(cudaMemsetAsync(plan[i].a.ctr, 0, sizeof(EdgeMapCtr), s), "edge-map counters");
+            KAIROS_CUDA(edgemap_launch(plan[i].a, lanes, g->lam_bits, grid, s), "edge-map launch");
+            if (direct && plan[i].host_src) {
+                const std::vector<int> &q = plan[i].qid;
+                for (size_t j = 0; j < q.size(); ++j)
+                    KAIROS_CUDA(cudaMemcpyAsync(out + (int64_t)q[j] * n, plan[i].host_src + (int64_t)j * n,
+                                                (size_t)n * 4, cudaMemcpyDeviceToHost, s),
                                 "copy labels to host");
-                }
-                KAIROS_CUDA(cudaStreamSynchronize(s), "copy labels to host");
             }
-            if (stats) {
-                for (int j = 0; j < k; ++j) {
-                    kairos_query_stats &S = stats[idx[c + j]];
-                    S.relaxed_edges = res.relaxed[j];
-                    S.scanned_edges = res.scanned;
-                    S.rounds = res.rounds;
-                    S.reached = res.reached[j];
+        }
+        return KAIROS_OK;
+    };
+
+    KAIROS_CUDA(cudaEventRecord(w.ev0, s), "event record");
+    const bool capturable = dev && s != nullptr && !getenv("KAIROS_NO_GRAPH");
+    bool launched = false;
+    if (capturable) {
+        // key: everything the captured launches depend on
+        std::string key((const char *)&grid, sizeof(grid));
+        for (const Planned &P : plan) key.append((const char *)&P.a, sizeof(EdgeMapArgs));
+        if (w.graph_exec && w.graph_key == key) {
+            KAIROS_CUDA(cudaGraphLaunch(w.graph_exec, s), "graph launch");
+            launched = true;
+            ++g->graph_launches;
+        } else {
+            drop_graph(g);
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const kairos_status est = enqueue(false);
+                const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                if (est == KAIROS_OK && ce == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&w.graph_exec, graph, 0) == cudaSuccess) {
+                    w.graph_key = key;
+                    KAIROS_CUDA(cudaGraphLaunch(w.graph_exec, s), "graph launch");
+                    launched = true;
+                    ++g->graph_launches;
                 }
+                if (graph) cudaGraphDestroy(graph);
+            }
+            cudaGetLastError();  // a failed capture falls back to direct launches
+        }
+    }
+    if (!launched) {
+        st = enqueue(true);
+        if (st != KAIROS_OK) return st;
+    }
+    KAIROS_CUDA(cudaEventRecord(w.ev1, s), "event record");
+    KAIROS_CUDA(cudaMemcpyAsync(w.ctrs_host, w.ctrs, plan.size() * sizeof(EdgeMapCtr), cudaMemcpyDeviceToHost, s),
+                "edge-map counters");
+    KAIROS_CUDA(cudaStreamSynchronize(s), "edge-map");
+    float ms = 0;
+    KAIROS_CUDA(cudaEventElapsedTime(&ms, w.ev0, w.ev1), "event time");
+    g->last_kernel_ms = ms;
+    g->last_launches = (int)plan.size();
+    std::memcpy(w.ctr_host, &w.ctrs_host[plan.size() - 1], sizeof(EdgeMapCtr));  // last launch, for diagnostics
+    for (size_t i = 0; i < plan.size(); ++i) {
+        const EdgeMapCtr &res = w.ctrs_host[i];
+        if (res.err) return ctr_error(res.err);
+        if (stats) {
+            for (size_t j = 0; j < plan[i].qid.size(); ++j) {
+                kairos_query_stats &S = stats[plan[i].qid[j]];
+                S.relaxed_edges = res.relaxed[j];
+                S.scanned_edges = res.scanned;
+                S.rounds = res.rounds;
+                S.reached = res.reached[j];
             }
         }
     }
@@ -407,6 +499,9 @@ void kairos_graph_free(kairos_graph *g) {
         free_csr(g->A, &g->rev);
         g->A.put(g->work.ctr);
         if (g->work.ctr_host) cudaFreeHost(g->work.ctr_host);
+        g->A.put(g->work.ctrs);
+        if (g->work.ctrs_host) cudaFreeHost(g->work.ctrs_host);
+        if (g->work.graph_exec) cudaGraphExecDestroy(g->work.graph_exec);
         if (g->work.ev0) cudaEventDestroy(g->work.ev0);
         if (g->work.ev1) cudaEventDestroy(g->work.ev1);
         cudaGetLastError();
@@ -426,6 +521,7 @@ kairos_status kairos_graph_get_info(const kairos_graph *g, kairos_graph_info *in
                          (g->fwd.fidx ? g->n * 4 : 0) + (g->rev.fidx ? g->n * 4 : 0) + (int64_t)g->work.bytes;
     info->build_ms = g->build_ms;
     info->index_ms = g->index_ms;
+    info->graph_launches = g->graph_launches;
     return KAIROS_OK;
 }
 

@@ -217,5 +217,12 @@ struct kairos_graph {
         uint32_t *stage = nullptr;              // [lanes][n] output staging for host outputs
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         size_t bytes = 0;
+        kairos::EdgeMapCtr *ctrs = nullptr;       // one counter slot per launch of a call
+        kairos::EdgeMapCtr *ctrs_host = nullptr;  // pinned mirror
+        size_t ctr_slots = 0;
+        cudaGraphExec_t graph_exec = nullptr;     // the last captured call
+        std::string graph_key;
     } work;
+    int last_launches = 0;
+    int64_t graph_launches = 0;
 };

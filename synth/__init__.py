@@ -283,10 +283,11 @@ def scaled(spec: GraphSpec, scale: int, m: int) -> GraphSpec:
     return replace(spec, scale=scale, m=m)
 
 
-def workload_queries(key: int, el: EdgeList, count: int | None = None) -> list[Query]:
-    """The query set of workload `key` drawn on edge list `el` (seed = graph seed + 0x100)."""
+def workload_queries(key: int, el: EdgeList, count: int | None = None, shard: int = 0) -> list[Query]:
+    """The query set of workload `key` drawn on edge list `el` (seed = graph seed + 0x100);
+    shard > 0 draws a disjointly seeded set of the same shape (one per replica)."""
     w = WORKLOADS[key]
-    seed = w.graph.seed + 0x100 + key
+    seed = w.graph.seed + 0x100 + key + 0x10000 * shard
     span = w.graph.t_span
     if key == 1:
         (s,) = pick_vertices(el, 1, seed, True, False)

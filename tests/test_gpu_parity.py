@@ -307,3 +307,30 @@ def test_device_wait_and_round_cap_return_timeout(tiny, monkeypatch):
     monkeypatch.delenv("KAIROS_ROUND_CAP")
     g.earliest_arrival(q.vertex, q.ta, q.tw, out)
     assert np.array_equal(labels(out), orc.query(q))
+
+
+def test_captured_batch_replays_and_recaptures(tiny):
+    """On a graph with its own stream and device outputs, a repeated batch is captured into
+    a CUDA graph and replayed; each replay recomputes the labels, and a different batch is
+    captured afresh."""
+    el, orc, _ = tiny
+    stream = torch.cuda.Stream()
+    g = kx.Graph.from_edges(el, stream=stream)
+    g.index(64)
+    g.set_tuning(lanes=8)
+    n = el.n
+    with torch.cuda.stream(stream):
+        for qs in (tiny_queries(el, 20), tiny_queries(el, 13)[::-1]):
+            out = torch.empty((len(qs), n), dtype=torch.int32, device="cuda")
+            want = [orc.query(q) for q in qs]
+            for rep in range(3):
+                out.fill_(0x5A5A5A5A)
+                stats = g.batch(qs, out, want_stats=(rep == 1))
+                got = labels(out)
+                for i in range(len(qs)):
+                    assert np.array_equal(got[i], want[i]), (rep, qs[i])
+                if rep == 1:
+                    assert [s.relaxed_edges for s in stats] == [orc.admissible(q, w) for q, w in zip(qs, want)]
+    torch.cuda.synchronize()
+    assert g.info().graph_launches == 6  # both batches, three calls each, ran as graphs
+    g.close()
