@@ -272,7 +272,7 @@ def test_medium_full_size_sampled_against_oracle(medium):
     certified at full size, and a sample is compared label by label with the oracle."""
     el, g = medium
     qs = synth.workload_queries(2, el)
-    g.set_tuning(lanes=8)
+    g.autotune(qs)  # the launch shape the benchmark times
     got, stats = gpu_batch(g, el.n, qs)
     orc = Oracle(el)
     for i in (0, 1, 63, 64, 65, 127):
