@@ -177,6 +177,14 @@ kairos_status kairos_set_tuning(kairos_graph *g, const kairos_tuning *t);
  * install the fastest; *best (may be NULL) receives it.  Errors as kairos_batch_query. */
 kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32_t n, kairos_tuning *best);
 
+/* Selective-index threshold by measurement (the cost model of Sec. 5.1 sets the cutoff
+ * experimentally): for each of the n_thetas candidates (KAIROS_NO_INDEX allowed) rebuild
+ * the fence level, time `sample` with the current launch shape, and keep the fastest.
+ * ms_out (may be NULL) receives each candidate's device time.  *best (may be NULL) gets the
+ * chosen threshold, which stays built.  Errors as kairos_batch_query / kairos_index_build. */
+kairos_status kairos_autotune_index(kairos_graph *g, const kairos_query *sample, int32_t n, const uint32_t *thetas,
+                                    int32_t n_thetas, uint32_t *best, double *ms_out);
+
 /* ---- continuous-batching server ------------------------------------------------------ */
 
 typedef struct {

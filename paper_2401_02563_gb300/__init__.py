@@ -103,6 +103,8 @@ SIGNATURES = {
     "kairos_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
     "kairos_autotune": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32,
                                        ctypes.POINTER(kairos_tuning)]),
+    "kairos_autotune_index": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32, _P, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_uint32), _P]),
     "kairos_serve_create": (ctypes.c_int, [_P, ctypes.POINTER(kairos_serve_opts), ctypes.POINTER(_P)]),
     "kairos_serve_submit": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), _P, ctypes.POINTER(ctypes.c_uint64)]),
     "kairos_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(kairos_result_info)]),
@@ -320,6 +322,17 @@ def kairos_autotune(g, sample) -> kairos_tuning:
     return best
 
 
+def kairos_autotune_index(g, sample, thetas):
+    """Pick the index threshold among `thetas` by timing `sample`; returns (best, {theta: ms})."""
+    qarr, k = make_queries(sample)
+    th = np.ascontiguousarray(np.array([int(x) & 0xFFFFFFFF for x in thetas], np.uint32))
+    ms = np.zeros(len(th), np.float64)
+    best = ctypes.c_uint32(0)
+    _check(lib().kairos_autotune_index(g, qarr, k, th.ctypes.data, len(th), ctypes.byref(best), ms.ctypes.data),
+           "kairos_autotune_index")
+    return int(best.value), dict(zip(th.tolist(), ms.tolist()))
+
+
 def kairos_serve_create(g, max_slots=0, queue_capacity=0, reserve_bytes=0, rounds_per_slice=0):
     opts = kairos_serve_opts(int(max_slots), int(queue_capacity), int(reserve_bytes), int(rounds_per_slice))
     h = _P()
@@ -412,6 +425,9 @@ class Graph:
 
     def autotune(self, sample):
         return kairos_autotune(self.handle, sample)
+
+    def autotune_index(self, sample, thetas=(16, 64, 256, 1024, 4096, KAIROS_NO_INDEX)):
+        return kairos_autotune_index(self.handle, sample, thetas)
 
     def info(self):
         return kairos_graph_get_info(self.handle)

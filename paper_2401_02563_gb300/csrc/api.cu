@@ -624,6 +624,34 @@ kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32
     return KAIROS_OK;
 }
 
+kairos_status kairos_autotune_index(kairos_graph *g, const kairos_query *sample, int32_t n, const uint32_t *thetas,
+                                    int32_t n_thetas, uint32_t *best, double *ms_out) {
+    if (!g || !sample || n <= 0 || !thetas || n_thetas <= 0) return fail(KAIROS_ERR_INVALID_ARG, "autotune index: bad argument");
+    for (int i = 0; i < n; ++i) {
+        kairos_status st = check_query(g, sample[i]);
+        if (st != KAIROS_OK) return st;
+    }
+    uint32_t win = KAIROS_NO_INDEX;
+    double win_ms = -1;
+    for (int k = 0; k < n_thetas; ++k) {
+        kairos_status st = kairos_index_build(g, thetas[k]);
+        if (st != KAIROS_OK) return st;
+        std::lock_guard<std::mutex> lk(g->mu);
+        st = kairos_run_queries(g, sample, n, nullptr, nullptr, g->tuning.lanes);
+        if (st != KAIROS_OK) return st;
+        const double ms = g->last_kernel_ms;
+        if (ms_out) ms_out[k] = ms;
+        if (win_ms < 0 || ms < win_ms) {
+            win_ms = ms;
+            win = thetas[k];
+        }
+    }
+    kairos_status st = kairos_index_build(g, win);
+    if (st != KAIROS_OK) return st;
+    if (best) *best = win;
+    return KAIROS_OK;
+}
+
 const char *kairos_last_error(void) { return g_err.c_str(); }
 
 const char *kairos_status_string(kairos_status s) {
