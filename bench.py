@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--serve-rates", default="1000,4000,16000")
     p.add_argument("--serve-queries", type=int, default=400)
+    p.add_argument("--serve-slots", type=int, default=16)
+    p.add_argument("--serve-slice", type=int, default=0, help="edge-map rounds per server launch (0: default)")
     return p.parse_args()
 
 
@@ -156,15 +158,15 @@ def serve_stream(el, span, count, seed):
             for q, (k, (ta, tw)) in enumerate(zip(kinds, wins))]
 
 
-def measure_serving(torch, kx, g, el, span, rates, per_rate, slots):
+def measure_serving(torch, kx, g, el, span, rates, per_rate, slots, slice_rounds=0):
     """Open-loop Poisson arrivals at each rate through kairos_serve_submit/poll; latency is
     the server's submit-to-completion time.  The same stream is also answered one query
     per launch (kairos_earliest_arrival / kairos_latest_departure, FIFO) for comparison."""
     import threading
     n = el.n
     pool = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(256)]
-    res = {"slots_per_kind": slots, "queries_per_rate": per_rate, "rates": []}
-    server = kx.kairos_serve_create(g.handle, max_slots=slots)
+    res = {"slots_per_kind": slots, "rounds_per_slice": slice_rounds or 2, "queries_per_rate": per_rate, "rates": []}
+    server = kx.kairos_serve_create(g.handle, max_slots=slots, rounds_per_slice=slice_rounds)
     try:
         for ri, rate in enumerate(rates):
             qs = serve_stream(el, span, per_rate, 0x5E7E + ri)
@@ -431,7 +433,8 @@ def main():
             if args.workload == 4 and args.serve_rates == "1000,4000,16000":
                 args.serve_rates = "1000,3000,10000,30000,100000"
             rates = [float(x) for x in args.serve_rates.split(",") if x]
-            served = measure_serving(torch, kx, g, el, w.graph.t_span, rates, args.serve_queries, 32)
+            served = measure_serving(torch, kx, g, el, w.graph.t_span, rates, args.serve_queries, args.serve_slots,
+                                     args.serve_slice)
         g.close()
 
     if rank != 0:

@@ -114,6 +114,13 @@ typedef struct {
     int32_t chunk_edges;    /* edges per grid-wide chunk of a split range (multiple of 32) */
     int32_t dense_div;      /* sweep the frontier bitmap instead of the queue when
                                |frontier| > n / dense_div (0: never) */
+    int32_t relax_mode;     /* 0: read the head's label and lower it only when the arrival is
+                               earlier, queueing heads that changed, fetching every lane
+                               segment of a head at once (suits many active lanes); 2: the same
+                               check, fetching only segments with candidate lanes, pass by pass
+                               (suits few active lanes); 1: lower it with a fire-and-forget
+                               atomic for every usable edge and take the next frontier from the
+                               bitmap of touched heads */
 } kairos_tuning;
 
 typedef struct {
@@ -189,12 +196,12 @@ kairos_status kairos_autotune_index(kairos_graph *g, const kairos_query *sample,
 
 typedef struct {
     int32_t max_slots;      /* queries resident at once per query kind (lanes of the running
-                               edge-map): 2, 4, 8, 16 or 32; 0: 32.  Lowered at start while the
+                               edge-map): 2, 4, 8, 16 or 32; 0: 16.  Lowered at start while the
                                device cannot hold that many beside reserve_bytes */
     int32_t queue_capacity; /* pending submissions before submit returns BUSY; 0: 4096 */
     int64_t reserve_bytes;  /* device memory to leave free; no query is admitted while free
                                memory is below it; 0: 256 MiB */
-    int32_t rounds_per_slice; /* edge-map rounds per launch between admissions; 0: 4 */
+    int32_t rounds_per_slice; /* edge-map rounds per launch between admissions; 0: 2 */
 } kairos_serve_opts;
 
 typedef struct {

@@ -196,6 +196,7 @@ EdgeMapArgs make_args(kairos_graph *g, const Csr &c, const LaneParams &lp, uint3
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;
     a.count_relaxed = count_relaxed;
+    a.relax_mode = g->tuning.relax_mode;
     a.resume = 0;
     a.round_begin = 0;
     a.round_end = 0xFFFFFFFFu;
@@ -575,6 +576,7 @@ kairos_status kairos_set_tuning(kairos_graph *g, const kairos_tuning *t) {
     if (t->chunk_edges < 32 || t->chunk_edges % 32 || t->chunk_edges > (1 << 24))
         return fail(KAIROS_ERR_INVALID_ARG, "tuning: chunk_edges a multiple of 32 in [32, 2^24]");
     if (t->dense_div < 0) return fail(KAIROS_ERR_INVALID_ARG, "tuning: dense_div >= 0");
+    if (t->relax_mode < 0 || t->relax_mode > 2) return fail(KAIROS_ERR_INVALID_ARG, "tuning: relax_mode is 0, 1 or 2");
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning = *t;
     return KAIROS_OK;
@@ -592,14 +594,18 @@ kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32
     double win_ms = -1;
     const int lanes_set[] = {1, 2, 4, 8, 16, 32};
     const int wmax_set[] = {32, 128, 512};
-    const int dense_set[] = {0, 16};
+    // {dense_div, relax_mode}: queue or bitmap frontier; all-segment, candidate-pass or
+    // unconditional relaxation
+    const int shape_set[][2] = {{0, 0}, {16, 0}, {0, 2}, {16, 2}, {0, 1}};
     for (int L : lanes_set) {
         for (int wm : wmax_set) {
-            for (int dd : dense_set) {
+            for (const auto &sh : shape_set) {
+                if (L == 1 && sh[1] == 2) continue;  // one lane: the two checked modes coincide
                 kairos_tuning c = base;
                 c.lanes = L;
                 c.warp_max_edges = wm;
-                c.dense_div = dd;
+                c.dense_div = sh[0];
+                c.relax_mode = sh[1];
                 g->tuning = c;
                 kairos_status st = kairos_run_queries(g, sample, n, nullptr, nullptr, L);
                 if (st == KAIROS_ERR_OOM) continue;  // this lane width does not fit: skip it

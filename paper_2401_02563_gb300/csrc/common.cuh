@@ -144,6 +144,7 @@ struct EdgeMapArgs {
     uint32_t max_rounds;
     int warp_max_edges, chunk_edges, dense_div;
     int count_relaxed;     // nonzero: count relaxations per lane (query statistics)
+    int relax_mode;        // 0 checked minimum + queue, 1 unconditional reductions + bitmap frontier
     // resumable operation: resume != 0 keeps the state of an earlier launch (no init, no
     // seeding, no readout) and runs rounds [round_begin, round_end); lanes outside
     // running_mask take no part
@@ -161,6 +162,15 @@ cudaError_t column_readout(const uint32_t *arr, int64_t n, int W, int q, int mir
                            unsigned long long *stats, cudaStream_t s);
 // Reset the lanes in mask to the unreached state (labels and scan bounds).
 cudaError_t column_reset(uint32_t *arr, uint32_t *prev, int64_t n, int W, uint32_t mask, cudaStream_t s);
+// Retire the lanes in mask in one pass over the vertices: lanes in write_mask get
+// out[q][v] = label (mirrored back when mirror_mask has q) with reached count and checksum
+// added to stats[2q], stats[2q+1]; every lane in mask is then reset to unreached.
+struct RetireArgs {
+    uint32_t *out[MAX_LANES];
+    uint32_t mask, write_mask, mirror_mask;
+};
+cudaError_t retire_lanes(uint32_t *arr, uint32_t *prev, int64_t n, int W, const RetireArgs &ra,
+                         unsigned long long *stats, cudaStream_t s);
 // Seed lane q at source src with label ta into the frontier of round r (bitmap + queue).
 cudaError_t seed_lane(const EdgeMapArgs &a, int W, int q, int32_t src, uint32_t ta, uint32_t r, cudaStream_t s);
 

@@ -286,6 +286,40 @@ __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)
                                         const uint32_t (&ll)[K_EDGES], ActF actf, BoundsF bounds, BlockSmem &B,
                                         unsigned long long &cnt1, int lane, int nxt, int n3, uint32_t &hit) {
     uint32_t mark = 0;  // bit k: edge k lowered its head in some lane
+    if (a.relax_mode == 1) {
+        // every usable edge lowers its head unconditionally (fire-and-forget) and marks it
+        // in the next bitmap (fire-and-forget): no load, no wait, no queue
+#pragma unroll
+        for (int k = 0; k < K_EDGES; ++k) {
+            if (d[k] < 0) continue;
+            const uint32_t tau = tt[k] + ll[k];
+            uint32_t cand = 0;
+            if constexpr (W == 1) {
+                uint32_t th, li;
+                bounds(k, 0, th, li);
+                cand = (actf(k) && th <= tt[k] && tt[k] < li && tau <= B.tw[0]) ? 1u : 0u;
+                cnt1 += cand;
+            } else {
+                uint32_t act = actf(k);
+                while (act) {
+                    const int q = __ffs(act) - 1;
+                    act &= act - 1;
+                    uint32_t th, li;
+                    bounds(k, q, th, li);
+                    if (th <= tt[k] && tt[k] < li && tau <= B.tw[q]) cand |= 1u << q;
+                }
+                if (a.count_relaxed)
+                    for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicAdd(&B.cnt[__ffs(c2) - 1], 1u);
+            }
+            if (cand) {
+                uint32_t *row = a.arr + (size_t)d[k] * W;
+                for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicMin(row + (__ffs(c2) - 1), tau);
+                atomicOr(&a.bm[nxt][d[k] >> 5], 1u << (d[k] & 31));
+                hit |= cand;
+            }
+        }
+        return;
+    }
     if constexpr (W == 1) {
         bool ok[K_EDGES];
         uint32_t cur[K_EDGES];
@@ -308,56 +342,130 @@ __device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)
             }
         }
     } else {
-        // candidate lanes of each edge from the time bounds, then the head's state-row
-        // segments holding them, fetched with independent vector loads
-        constexpr int SEG = (W >= 4) ? 4 : W;  // lanes per load
-        constexpr int NSEG = W / SEG;
-        constexpr uint32_t SEGMASK = (SEG == 32) ? 0xFFFFFFFFu : ((1u << SEG) - 1u);
-#pragma unroll
-        for (int k = 0; k < K_EDGES; ++k) {
-            uint32_t cand = 0;
-            const uint32_t tau = tt[k] + ll[k];
-            if (d[k] >= 0) {
-                uint32_t act = actf(k);
-                while (act) {
-                    const int q = __ffs(act) - 1;
-                    act &= act - 1;
-                    uint32_t th, li;
-                    bounds(k, q, th, li);
-                    if (th <= tt[k] && tt[k] < li && tau <= B.tw[q]) cand |= 1u << q;
+        if (a.relax_mode == 2) {
+            // candidate lanes of each edge from the time bounds alone (shared memory)
+            uint32_t cand_k[K_EDGES];
+    #pragma unroll
+            for (int k = 0; k < K_EDGES; ++k) {
+                uint32_t cand = 0;
+                const uint32_t tau = tt[k] + ll[k];
+                if (d[k] >= 0) {
+                    uint32_t act = actf(k);
+                    while (act) {
+                        const int q = __ffs(act) - 1;
+                        act &= act - 1;
+                        uint32_t th, li;
+                        bounds(k, q, th, li);
+                        if (th <= tt[k] && tt[k] < li && tau <= B.tw[q]) cand |= 1u << q;
+                    }
+                    if (a.count_relaxed)
+                        for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicAdd(&B.cnt[__ffs(c2) - 1], 1u);
                 }
-                if (a.count_relaxed)
-                    for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicAdd(&B.cnt[__ffs(c2) - 1], 1u);
+                cand_k[k] = cand;
             }
-            if (cand) {
-                uint32_t *row = a.arr + (size_t)d[k] * W;
-                uint32_t cur[W];
-#pragma unroll
-                for (int sg = 0; sg < NSEG; ++sg) {
-                    if ((cand >> (sg * SEG)) & SEGMASK) {
-                        if constexpr (SEG == 4) {
-                            const uint4 v = *reinterpret_cast<const uint4 *>(row + sg * 4);  // may be stale: never below
-                            cur[sg * 4] = v.x;
-                            cur[sg * 4 + 1] = v.y;
-                            cur[sg * 4 + 2] = v.z;
-                            cur[sg * 4 + 3] = v.w;
+            // the head-row segments holding candidates, one per edge per pass: every edge of the
+            // thread has a segment load in flight at once, and the passes stop when no edge has
+            // candidates left (cost follows the candidates, not the lane width)
+            constexpr int SEGL = (W >= 4) ? 4 : W;
+            uint32_t rem[K_EDGES];
+    #pragma unroll
+            for (int k = 0; k < K_EDGES; ++k) rem[k] = cand_k[k];
+            for (;;) {
+                bool any = false;
+                uint32_t v4[K_EDGES][SEGL];
+                int sgk[K_EDGES];
+    #pragma unroll
+                for (int k = 0; k < K_EDGES; ++k) {
+                    sgk[k] = -1;
+                    if (rem[k]) {
+                        any = true;
+                        const int sg = (__ffs(rem[k]) - 1) / SEGL;
+                        sgk[k] = sg;
+                        const uint32_t *row = a.arr + (size_t)d[k] * W + sg * SEGL;
+                        if constexpr (SEGL == 4) {
+                            const uint4 v = *reinterpret_cast<const uint4 *>(row);  // may be stale: never below
+                            v4[k][0] = v.x;
+                            v4[k][1] = v.y;
+                            v4[k][2] = v.z;
+                            v4[k][3] = v.w;
                         } else {
                             const uint2 v = *reinterpret_cast<const uint2 *>(row);
-                            cur[0] = v.x;
-                            cur[1] = v.y;
+                            v4[k][0] = v.x;
+                            v4[k][1] = v.y;
                         }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < SEG; ++j) cur[sg * SEG + j] = 0u;
                     }
                 }
-#pragma unroll
-                for (int q = 0; q < W; ++q)
-                    if (((cand >> q) & 1u) && tau < cur[q]) {
-                        atomicMin(row + q, tau);  // result unused: a reduction
-                        mark |= 1u << k;
-                        hit |= 1u << q;
+                if (!any) break;
+    #pragma unroll
+                for (int k = 0; k < K_EDGES; ++k) {
+                    if (sgk[k] < 0) continue;
+                    const uint32_t tau = tt[k] + ll[k];
+                    uint32_t *row = a.arr + (size_t)d[k] * W + sgk[k] * SEGL;
+    #pragma unroll
+                    for (int j = 0; j < SEGL; ++j) {
+                        const int q = sgk[k] * SEGL + j;
+                        if (((rem[k] >> q) & 1u) && tau < v4[k][j]) {
+                            atomicMin(row + j, tau);  // result unused: a reduction
+                            mark |= 1u << k;
+                            hit |= 1u << q;
+                        }
                     }
+                    const uint32_t segbits = (SEGL == 32) ? 0xFFFFFFFFu : (((1u << SEGL) - 1u) << (sgk[k] * SEGL));
+                    rem[k] &= ~segbits;
+                }
+            }
+        } else {
+            // candidate lanes of each edge from the time bounds, then the head's state-row
+            // segments holding them, fetched with independent vector loads
+            constexpr int SEG = (W >= 4) ? 4 : W;  // lanes per load
+            constexpr int NSEG = W / SEG;
+            constexpr uint32_t SEGMASK = (SEG == 32) ? 0xFFFFFFFFu : ((1u << SEG) - 1u);
+    #pragma unroll
+            for (int k = 0; k < K_EDGES; ++k) {
+                uint32_t cand = 0;
+                const uint32_t tau = tt[k] + ll[k];
+                if (d[k] >= 0) {
+                    uint32_t act = actf(k);
+                    while (act) {
+                        const int q = __ffs(act) - 1;
+                        act &= act - 1;
+                        uint32_t th, li;
+                        bounds(k, q, th, li);
+                        if (th <= tt[k] && tt[k] < li && tau <= B.tw[q]) cand |= 1u << q;
+                    }
+                    if (a.count_relaxed)
+                        for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicAdd(&B.cnt[__ffs(c2) - 1], 1u);
+                }
+                if (cand) {
+                    uint32_t *row = a.arr + (size_t)d[k] * W;
+                    uint32_t cur[W];
+    #pragma unroll
+                    for (int sg = 0; sg < NSEG; ++sg) {
+                        if ((cand >> (sg * SEG)) & SEGMASK) {
+                            if constexpr (SEG == 4) {
+                                const uint4 v = *reinterpret_cast<const uint4 *>(row + sg * 4);  // may be stale: never below
+                                cur[sg * 4] = v.x;
+                                cur[sg * 4 + 1] = v.y;
+                                cur[sg * 4 + 2] = v.z;
+                                cur[sg * 4 + 3] = v.w;
+                            } else {
+                                const uint2 v = *reinterpret_cast<const uint2 *>(row);
+                                cur[0] = v.x;
+                                cur[1] = v.y;
+                            }
+                        } else {
+    #pragma unroll
+                            for (int j = 0; j < SEG; ++j) cur[sg * SEG + j] = 0u;
+                        }
+                    }
+    #pragma unroll
+                    for (int q = 0; q < W; ++q)
+                        if (((cand >> q) & 1u) && tau < cur[q]) {
+                            atomicMin(row + q, tau);  // result unused: a reduction
+                            mark |= 1u << k;
+                            hit |= 1u << q;
+                        }
+                }
             }
         }
     }
@@ -570,7 +678,10 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
         uint32_t hit = 0;  // lanes this thread lowered a label in, this round
         const int cur = r & 1, nxt = cur ^ 1;
         const int c3 = r % 3, n3 = (r + 1) % 3, p3 = (r + 2) % 3;
-        const unsigned F = __ldcg(&C->qcount[c3].v);
+        // relax_mode 1 keeps no queue: after round 0 the bitmap is the frontier, and a round
+        // without usable edges in any lane (active mask 0) ends the launch
+        const unsigned F = (a.relax_mode == 1 && r > 0) ? (__ldcg(&C->active[p3].v) ? 1u : 0u)
+                                                        : __ldcg(&C->qcount[c3].v);
         if (tid == 0 && r <= PROFILE_ROUNDS) {
             C->round_ns[r] = globaltimer();
             if (r > 0) C->round_chunks[r - 1] = __ldcg(&C->chunks[(r + 2) % 3].v);
@@ -590,7 +701,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(c
             C->bdone[n3].v = 0;
             C->active[n3].v = 0;
         }
-        const bool dense = a.dense_div > 0 && (int64_t)F * a.dense_div > n;
+        const bool dense = a.relax_mode == 1 || (a.dense_div > 0 && (int64_t)F * a.dense_div > n);
         // work of the round: batches of 32 queued vertices (or 1024-vertex bitmap stripes),
         // then the chunks that expanding them registered; both claimed dynamically
         const unsigned nb = dense ? (unsigned)((nwords + 31) / 32) : (F + 31) / 32;
@@ -876,6 +987,56 @@ __global__ void column_reset_kernel(uint32_t *arr, uint32_t *prev, int64_t n, in
     }
 }
 
+// One warp per 32 vertices and lane (the lane loop is uniform); per-lane sums gather in
+// shared memory and leave with one atomic per block.
+__global__ void retire_lanes_kernel(uint32_t *arr, uint32_t *prev, int64_t n, int W, const RetireArgs ra,
+                                    unsigned long long *stats) {
+    __shared__ unsigned long long s_cnt[MAX_LANES], s_cs[MAX_LANES];
+    if (threadIdx.x < MAX_LANES) {
+        s_cnt[threadIdx.x] = 0;
+        s_cs[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + threadIdx.x;
+        for (uint32_t m = ra.mask; m; m &= m - 1) {
+            const int q = __ffs(m) - 1;
+            unsigned long long cnt = 0, cs = 0;
+            if (v < n) {
+                const size_t i = (size_t)v * W + q;
+                const uint32_t x = arr[i];
+                if ((ra.write_mask >> q) & 1u) {
+                    const uint32_t y = (((ra.mirror_mask >> q) & 1u) && x != INF) ? TMAX - x : x;
+                    ra.out[q][v] = y;
+                    cnt = (x != INF);
+                    cs = (unsigned long long)(v + 1) * y;
+                }
+                // only a vertex the query reached can hold a label or a scan bound (a bound
+                // is set only when a reached vertex is expanded): reset just those
+                if (x != INF) {
+                    arr[i] = INF;
+                    prev[i] = INF;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                cnt += __shfl_xor_sync(FULL, cnt, o);
+                cs += __shfl_xor_sync(FULL, cs, o);
+            }
+            if (lane == 0 && ((ra.write_mask >> q) & 1u)) {
+                atomicAdd(&s_cnt[q], cnt);
+                atomicAdd(&s_cs[q], cs);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < MAX_LANES && ((ra.write_mask >> threadIdx.x) & 1u)) {
+        atomicAdd(&stats[2 * threadIdx.x], s_cnt[threadIdx.x]);
+        atomicAdd(&stats[2 * threadIdx.x + 1], s_cs[threadIdx.x]);
+    }
+}
+
 // Lane q's source enters the frontier of round r: its label, then the bitmap bit and a
 // queue slot unless the vertex is already queued for that round.
 __global__ void seed_lane_kernel(uint32_t *arr, uint32_t *bm, int32_t *queue, unsigned *count, int W, int q,
@@ -897,6 +1058,13 @@ cudaError_t column_readout(const uint32_t *arr, int64_t n, int W, int q, int mir
 cudaError_t column_reset(uint32_t *arr, uint32_t *prev, int64_t n, int W, uint32_t mask, cudaStream_t s) {
     const int grid = (int)std::min<int64_t>((n * W + 255) / 256, 8192);
     column_reset_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(arr, prev, n, W, mask);
+    return cudaGetLastError();
+}
+
+cudaError_t retire_lanes(uint32_t *arr, uint32_t *prev, int64_t n, int W, const RetireArgs &ra,
+                         unsigned long long *stats, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    retire_lanes_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(arr, prev, n, W, ra, stats);
     return cudaGetLastError();
 }
 

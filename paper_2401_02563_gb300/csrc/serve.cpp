@@ -18,6 +18,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -66,11 +68,11 @@ struct Session {
 
 struct kairos_server {
     kairos_graph *g = nullptr;
-    int slots = 32;
+    int slots = 16;
     int capacity = 4096;
     int64_t reserve = 256LL << 20;
-    int slice = 4;
-    cudaStream_t copy_stream = nullptr;
+    int slice = 2;
+    FILE *log = nullptr;  // KAIROS_SERVE_LOG: one line per session step (diagnostics)
     Session sess[2];
     std::thread th;
     std::mutex mu;
@@ -172,6 +174,9 @@ EdgeMapArgs session_args(kairos_graph *g, Session &S) {
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;
     a.count_relaxed = 1;
+    // resumable slices keep the queue frontier; served mixes have few active lanes per
+    // vertex, so only the state segments holding candidate lanes are read
+    a.relax_mode = 2;
     a.running_mask = S.running;
     return a;
 }
@@ -218,9 +223,7 @@ kairos_status step_session(kairos_server *V, Session &S, std::vector<std::pair<u
         for (int q = 0; q < MAX_LANES; ++q) S.relaxed_base[q] = 0;
         a.resume = 0;  // the kernel initialises every lane and seeds the running ones
     } else {
-        a.resume = 1;
-        const uint32_t newcols = seeds;
-        if (newcols) KAIROS_CUDA(column_reset(S.arr, S.prev, g->n, S.W, newcols, s), "serve: reset lanes");
+        a.resume = 1;  // retired lanes were reset to unreached when they were read out
         for (int q = 0; q < S.W; ++q)
             if ((seeds >> q) & 1u)
                 KAIROS_CUDA(seed_lane(a, S.W, q, S.lp.src[q], S.lp.ta[q], S.r, s), "serve: seed lane");
@@ -233,9 +236,11 @@ kairos_status step_session(kairos_server *V, Session &S, std::vector<std::pair<u
     int grid = edgemap_max_grid(S.W, g->lam_bits, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "serve: no resident launch shape");
     if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
+    const auto t_launch = clk::now();
     KAIROS_CUDA(edgemap_launch(a, S.W, g->lam_bits, grid, s), "serve: edge-map launch");
     KAIROS_CUDA(cudaMemcpyAsync(S.ctr_host, S.ctr, sizeof(EdgeMapCtr), cudaMemcpyDeviceToHost, s), "serve: counters");
     KAIROS_CUDA(cudaStreamSynchronize(s), "serve: edge-map");
+    const double launch_ms = std::chrono::duration<double, std::milli>(clk::now() - t_launch).count();
     S.fresh = false;
     S.pending_seed = 0;
     const EdgeMapCtr &c = *S.ctr_host;
@@ -258,8 +263,17 @@ kairos_status step_session(kairos_server *V, Session &S, std::vector<std::pair<u
         if (((S.running & ~finished) >> q) & 1u && (uint64_t)(S.r - S.admitted_round[q]) > (uint64_t)g->n + 1)
             timed_out |= 1u << q;
     finished |= timed_out;
+    if (V->log)
+        fprintf(V->log, "kind=%d r=%u running=%u seeded=%u finished=%u launch_ms=%.3f\n", S.kind, S.r,
+                (unsigned)__builtin_popcount(S.running), (unsigned)__builtin_popcount(seeds),
+                (unsigned)__builtin_popcount(finished), launch_ms);
     if (!finished) return KAIROS_OK;
     KAIROS_CUDA(cudaMemsetAsync(S.stats, 0, (size_t)MAX_LANES * 16, s), "serve: readout stats");
+    // one pass reads out every finished lane and resets it for its next query
+    RetireArgs ra;
+    std::memset(&ra, 0, sizeof(ra));
+    ra.mask = finished;
+    ra.mirror_mask = S.lp.mirror_mask;
     std::vector<std::pair<int, uint32_t *>> to_host;
     for (int q = 0; q < S.W; ++q) {
         if (!((finished >> q) & 1u) || ((timed_out >> q) & 1u)) continue;
@@ -271,11 +285,11 @@ kairos_status step_session(kairos_server *V, Session &S, std::vector<std::pair<u
             dst = T.out;
             on_dev = T.out_on_device;
         }
-        uint32_t *target = on_dev ? dst : S.stage + (int64_t)q * g->n;
-        KAIROS_CUDA(column_readout(S.arr, g->n, S.W, q, (S.lp.mirror_mask >> q) & 1u, target, S.stats + 2 * q, s),
-                    "serve: readout");
+        ra.out[q] = on_dev ? dst : S.stage + (int64_t)q * g->n;
+        ra.write_mask |= 1u << q;
         if (!on_dev) to_host.emplace_back(q, dst);
     }
+    KAIROS_CUDA(retire_lanes(S.arr, S.prev, g->n, S.W, ra, S.stats, s), "serve: retire lanes");
     for (auto &h : to_host)
         KAIROS_CUDA(cudaMemcpyAsync(h.second, S.stage + (int64_t)h.first * g->n, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s),
                     "serve: deliver result");
@@ -425,6 +439,7 @@ kairos_status kairos_serve_create(kairos_graph *g, const kairos_serve_opts *opts
             }
         }
     }
+    if (const char *path = getenv("KAIROS_SERVE_LOG")) V->log = fopen(path, "a");
     try {
         V->th = std::thread(worker, V);
     } catch (...) {
@@ -490,6 +505,7 @@ void kairos_serve_destroy(kairos_server *V) {
         free_session(V->g->A, V->sess[0]);
         free_session(V->g->A, V->sess[1]);
     }
+    if (V->log) fclose(V->log);
     delete V;
 }
 

@@ -334,3 +334,30 @@ def test_captured_batch_replays_and_recaptures(tiny):
     torch.cuda.synchronize()
     assert g.info().graph_launches == 6  # both batches, three calls each, ran as graphs
     g.close()
+
+
+@pytest.mark.parametrize("lanes,mode", [(1, 1), (2, 1), (8, 1), (32, 1), (2, 2), (4, 2), (16, 2), (32, 2)])
+def test_relax_modes(tiny, lanes, mode):
+    """relax_mode 1 (unconditional fire-and-forget minima, bitmap frontier) and 2 (checked
+    minima over candidate segments only) give the same labels and counts, including zero
+    durations and both predicates."""
+    el, orc, g = tiny
+    g.index(16)
+    g.set_tuning(lanes=lanes, relax_mode=mode, warp_max_edges=64, chunk_edges=64)
+    qs = tiny_queries(el, 21)
+    got, stats = gpu_batch(g, el.n, qs)
+    for i, q in enumerate(qs):
+        want = orc.query(q)
+        assert np.array_equal(got[i], want), q
+        assert stats[i].relaxed_edges == orc.admissible(q, want)
+    el2 = synth.random_small(90, 900, 0x9600 + lanes, t_max=30, lam_max=3, lam_min=0)
+    orc2 = Oracle(el2)
+    g2 = kx.Graph.from_edges(el2)
+    g2.index(4)
+    g2.set_tuning(lanes=lanes, relax_mode=mode)
+    qs2 = [Query(i % 2, (7 * i) % 90, i % 5, 20 + i % 13, (i // 2) % 2) for i in range(24)]
+    got2, _ = gpu_batch(g2, el2.n, qs2)
+    for i, q in enumerate(qs2):
+        assert np.array_equal(got2[i], orc2.query(q)), q
+    g2.close()
+    g.set_tuning(lanes=1, relax_mode=0, warp_max_edges=128, chunk_edges=512)
