@@ -621,7 +621,7 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, Blo
 }
 
 template <int W, typename LamT>
-__global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : 2)) edgemap_kernel(const EdgeMapArgs a) {
+__global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : (W == 32 ? 2 : 3))) edgemap_kernel(const EdgeMapArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockSmem B;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
