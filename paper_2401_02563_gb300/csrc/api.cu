@@ -21,8 +21,6 @@ namespace {
 thread_local std::string g_err;
 }
 
-void set_error(const std::string &m) { g_err = m; }
-
 kairos_status fail(kairos_status st, const std::string &m) {
     g_err = m;
     return st;
@@ -422,8 +420,6 @@ kairos_status kairos_graph_build(const kairos_edge_list *el, const kairos_graph_
     if (e == cudaSuccess) e = cudaEventCreate(&g->work.ev1);
     if (e == cudaSuccess) e = cudaMallocHost(&g->work.ctr_host, sizeof(EdgeMapCtr));
     if (e != cudaSuccess) return bail(cuda_fail(e, "graph build: setup"));
-    g->work.ctr = (EdgeMapCtr *)g->A.get(sizeof(EdgeMapCtr));
-    if (!g->work.ctr) return bail(fail(KAIROS_ERR_OOM, "graph build: device allocation failed"));
 
     const size_t lam_sz = el->lambda_bits == 16 ? 2 : 4;
     const int32_t *src = el->src, *dst = el->dst;
@@ -498,7 +494,6 @@ void kairos_graph_free(kairos_graph *g) {
         release_work_arrays(g);
         free_csr(g->A, &g->fwd);
         free_csr(g->A, &g->rev);
-        g->A.put(g->work.ctr);
         if (g->work.ctr_host) cudaFreeHost(g->work.ctr_host);
         g->A.put(g->work.ctrs);
         if (g->work.ctrs_host) cudaFreeHost(g->work.ctrs_host);

@@ -29,7 +29,6 @@ constexpr uint32_t NO_OWNER = 0xFFFFFFFFu;  // chunk_owner entry not yet publish
 
 // ---- status / error plumbing ---------------------------------------------------------
 
-void set_error(const std::string &msg);
 kairos_status fail(kairos_status st, const std::string &msg);
 kairos_status cuda_fail(cudaError_t e, const char *what);
 
@@ -156,12 +155,6 @@ struct EdgeMapArgs {
 };
 
 // Between resumable launches (serving): column operations on the [n][W] state.
-// Read lane q's labels into out (mirrored back when mirror), adding the reached count and
-// sum of (v + 1) * label to stats[0..1].
-cudaError_t column_readout(const uint32_t *arr, int64_t n, int W, int q, int mirror, uint32_t *out,
-                           unsigned long long *stats, cudaStream_t s);
-// Reset the lanes in mask to the unreached state (labels and scan bounds).
-cudaError_t column_reset(uint32_t *arr, uint32_t *prev, int64_t n, int W, uint32_t mask, cudaStream_t s);
 // Retire the lanes in mask in one pass over the vertices: lanes in write_mask get
 // out[q][v] = label (mirrored back when mirror_mask has q) with reached count and checksum
 // added to stats[2q], stats[2q+1]; every lane in mask is then reset to unreached.
@@ -178,7 +171,6 @@ cudaError_t seed_lane(const EdgeMapArgs &a, int W, int q, int32_t src, uint32_t 
 cudaError_t edgemap_launch(const EdgeMapArgs &a, int lanes, int lam_bits, int grid, cudaStream_t s);
 // Largest co-resident grid for this lane width (blocks per SM * SMs), 0 on error.
 int edgemap_max_grid(int lanes, int lam_bits, int *blocks_per_sm_out);
-size_t edgemap_smem_bytes(int lanes);
 
 // ---- device build ------------------------------------------------------------------------
 
@@ -222,8 +214,7 @@ struct kairos_graph {
         uint32_t *bigb = nullptr, *chunk_owner = nullptr;
         uint32_t cap_big = 0, cap_chunks = 0;
         int warp_max = 0, chunk = 0;
-        kairos::EdgeMapCtr *ctr = nullptr;      // device
-        kairos::EdgeMapCtr *ctr_host = nullptr; // pinned mirror
+        kairos::EdgeMapCtr *ctr_host = nullptr; // pinned copy of the last launch's counters (diagnostics)
         uint32_t *stage = nullptr;              // [lanes][n] output staging for host outputs
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         size_t bytes = 0;

@@ -956,37 +956,6 @@ int max_blocks_l(int lanes) {
     }
 }
 
-__global__ void column_readout_kernel(const uint32_t *arr, int64_t n, int W, int q, int mirror, uint32_t *out,
-                                      unsigned long long *stats) {
-    unsigned long long cnt = 0, cs = 0;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t x = arr[v * W + q];
-        const uint32_t y = (mirror && x != INF) ? TMAX - x : x;
-        out[v] = y;
-        cnt += (x != INF);
-        cs += (unsigned long long)(v + 1) * y;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        cnt += __shfl_xor_sync(FULL, cnt, o);
-        cs += __shfl_xor_sync(FULL, cs, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&stats[0], cnt);
-        atomicAdd(&stats[1], cs);
-    }
-}
-
-__global__ void column_reset_kernel(uint32_t *arr, uint32_t *prev, int64_t n, int W, uint32_t mask) {
-    const int64_t total = n * W;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        if ((mask >> (int)(i % W)) & 1u) {
-            arr[i] = INF;
-            prev[i] = INF;
-        }
-    }
-}
-
 // One warp per 32 vertices and lane (the lane loop is uniform); per-lane sums gather in
 // shared memory and leave with one atomic per block.
 __global__ void retire_lanes_kernel(uint32_t *arr, uint32_t *prev, int64_t n, int W, const RetireArgs ra,
@@ -1048,19 +1017,6 @@ __global__ void seed_lane_kernel(uint32_t *arr, uint32_t *bm, int32_t *queue, un
 
 }  // namespace
 
-cudaError_t column_readout(const uint32_t *arr, int64_t n, int W, int q, int mirror, uint32_t *out,
-                           unsigned long long *stats, cudaStream_t s) {
-    const int grid = (int)std::min<int64_t>((n + 255) / 256, 2048);
-    column_readout_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(arr, n, W, q, mirror, out, stats);
-    return cudaGetLastError();
-}
-
-cudaError_t column_reset(uint32_t *arr, uint32_t *prev, int64_t n, int W, uint32_t mask, cudaStream_t s) {
-    const int grid = (int)std::min<int64_t>((n * W + 255) / 256, 8192);
-    column_reset_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(arr, prev, n, W, mask);
-    return cudaGetLastError();
-}
-
 cudaError_t retire_lanes(uint32_t *arr, uint32_t *prev, int64_t n, int W, const RetireArgs &ra,
                          unsigned long long *stats, cudaStream_t s) {
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
@@ -1071,18 +1027,6 @@ cudaError_t retire_lanes(uint32_t *arr, uint32_t *prev, int64_t n, int W, const 
 cudaError_t seed_lane(const EdgeMapArgs &a, int W, int q, int32_t src, uint32_t ta, uint32_t r, cudaStream_t s) {
     seed_lane_kernel<<<1, 1, 0, s>>>(a.arr, a.bm[r & 1], a.queue[r & 1], &a.ctr->qcount[r % 3].v, W, q, src, ta);
     return cudaGetLastError();
-}
-
-size_t edgemap_smem_bytes(int lanes) {
-    switch (lanes) {
-        case 1: return sizeof(WarpSmem<1>) * (EM_THREADS / 32);
-        case 2: return sizeof(WarpSmem<2>) * (EM_THREADS / 32);
-        case 4: return sizeof(WarpSmem<4>) * (EM_THREADS / 32);
-        case 8: return sizeof(WarpSmem<8>) * (EM_THREADS / 32);
-        case 16: return sizeof(WarpSmem<16>) * (EM_THREADS / 32);
-        case 32: return sizeof(WarpSmem<32>) * (EM_THREADS / 32);
-        default: return 0;
-    }
 }
 
 cudaError_t edgemap_launch(const EdgeMapArgs &a, int lanes, int lam_bits, int grid, cudaStream_t s) {
