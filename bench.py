@@ -450,7 +450,8 @@ def main():
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": f"{w.name}: {w.description}", "vertices": n, "edges": m, "queries_per_step": Q,
                    "index_threshold": theta_now, "lanes": lanes, "warp_max_edges": tuning.warp_max_edges,
-                   "dense_div": tuning.dense_div, "parallelism": f"replicas x{world}",
+                   "chunk_edges": tuning.chunk_edges, "blocks_per_sm": tuning.blocks_per_sm,
+                   "relax_mode": tuning.relax_mode, "dense_div": tuning.dense_div, "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (graph {2 * (m * R + 8 * n) / 1e9:.1f} GB)"},
         "queries_per_s": world * Q / (step_ms / 1e3),
         "relaxed_edges_per_step": te_step, "scanned_edges_per_step": scanned_step,

@@ -620,6 +620,38 @@ kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32
         g->tuning = base;
         return fail(KAIROS_ERR_OOM, "autotune: no launch shape fits in device memory");
     }
+    // coordinate descent on the winner: chunk size, then resident blocks per SM
+    auto try_shape = [&](const kairos_tuning &c) -> kairos_status {
+        g->tuning = c;
+        kairos_status st = kairos_run_queries(g, sample, n, nullptr, nullptr, c.lanes);
+        if (st == KAIROS_ERR_OOM) return KAIROS_OK;
+        if (st != KAIROS_OK) return st;
+        if (g->last_kernel_ms < win_ms) {
+            win_ms = g->last_kernel_ms;
+            win = c;
+        }
+        return KAIROS_OK;
+    };
+    for (int ch : {256, 1024, 2048}) {
+        kairos_tuning c = win;
+        c.chunk_edges = ch;
+        kairos_status st = try_shape(c);
+        if (st != KAIROS_OK) {
+            g->tuning = base;
+            return st;
+        }
+    }
+    int bps = 0;
+    edgemap_max_grid(win.lanes, g->lam_bits, &bps);
+    for (int b = 1; b < bps; ++b) {
+        kairos_tuning c = win;
+        c.blocks_per_sm = b;
+        kairos_status st = try_shape(c);
+        if (st != KAIROS_OK) {
+            g->tuning = base;
+            return st;
+        }
+    }
     g->tuning = win;
     if (best) *best = win;
     return KAIROS_OK;
