@@ -300,7 +300,7 @@ kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_
     if (st != KAIROS_OK) return st;
     for (size_t i = 0; i < plan.size(); ++i) plan[i].a.ctr = w.ctrs + i;
     int bps = 0;
-    int grid = edgemap_max_grid(lanes, g->lam_bits, &bps);
+    int grid = edgemap_max_grid(lanes, g->lam_bits, g->tuning.relax_mode, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "edge-map: no resident launch shape (occupancy query failed)");
     if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
 
@@ -642,7 +642,7 @@ kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32
         }
     }
     int bps = 0;
-    edgemap_max_grid(win.lanes, g->lam_bits, &bps);
+    edgemap_max_grid(win.lanes, g->lam_bits, win.relax_mode, &bps);
     for (int b = 1; b < bps; ++b) {
         kairos_tuning c = win;
         c.blocks_per_sm = b;

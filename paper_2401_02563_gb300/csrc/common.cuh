@@ -170,7 +170,12 @@ cudaError_t seed_lane(const EdgeMapArgs &a, int W, int q, int32_t src, uint32_t 
 // Launch one persistent edge-map (cooperative: every block resident).
 cudaError_t edgemap_launch(const EdgeMapArgs &a, int lanes, int lam_bits, int grid, cudaStream_t s);
 // Largest co-resident grid for this lane width (blocks per SM * SMs), 0 on error.
-int edgemap_max_grid(int lanes, int lam_bits, int *blocks_per_sm_out);
+int edgemap_max_grid(int lanes, int lam_bits, int relax_mode, int *blocks_per_sm_out);
+// per lane width (defined in edgemap_kernel.cuh, instantiated in edgemap_w<W>.cu)
+template <int W>
+cudaError_t edgemap_launch_w(const EdgeMapArgs &a, int lam_bits, int grid, cudaStream_t s);
+template <int W>
+int edgemap_max_blocks_w(int lam_bits, int relax_mode);
 
 // ---- device build ------------------------------------------------------------------------
 

@@ -1,31 +1,5 @@
-// The temporal edge-map (Table 2 TemporalEdgeMap, Sec. 4.4) behind earliest arrival
-// (Alg. 2), as one persistent cooperative kernel per batch of W query lanes.
-//
-// State, vertex-major so that one edge feeds the W lanes of its head through contiguous
-// words:  arr[v][q]  the label of v in lane q (Alg. 2's t[]), and
-//         prev[v][q] the departure bound from which v's list was last scanned in lane q.
-// Round r (Alg. 2's while loop): for every frontier vertex u, each lane q with
-// thr = arr[u][q] (+1 under StrictlySucceeds, except at the lane's source) below
-// lim = min(prev[u][q], tw_q + 1) relaxes exactly the edges (u, v, t, lam) with
-// thr <= t < lim and t + lam <= tw_q: arr[v][q] = min(arr[v][q], t + lam) (Update's
-// writeMin).  Since the relaxed value does not depend on arr[u], each edge is relaxed at
-// most once per lane (prev[u][q] = thr afterwards).  The next frontier is every vertex
-// whose label dropped in some lane (the label-correcting reading of Alg. 2's Visited
-// flag), deduplicated by a bitmap and appended to a queue by warp ballots.
-//
-// Selective index (Sec. 3.2, Eqs. 1-3): a vertex with a fence level finds the first edge
-// at or after min_q thr and the end of the window by binary search (fence keys, then one
-// 32-edge block); an unindexed vertex scans its whole list, filtering by time.
-//
-// Work shapes: a warp takes 32 frontier vertices and gathers their W lane states with
-// coalesced row loads (thread per lane), keeping per vertex the mask of lanes with work.
-// Edges are then thread-per-edge, K_EDGES independent edges per thread per step (coalesced
-// loads, several misses in flight), each looping over its source's active lanes only.
-// Ranges up to warp_max_edges are walked by the warp that found them, concatenated;
-// longer ones are cut into chunk_edges chunks.  Within a round, warps claim batches of 32
-// frontier vertices from a counter and, once none is left, claim chunks as they are
-// published (release/acquire on the chunk's owner word), so one grid barrier ends the
-// round.  Large frontiers are swept from the bitmap in vertex order.
+// Launch dispatch of the temporal edge-map kernels (one instantiation file per lane width)
+// and the small kernels of resumable launches: retiring lanes and seeding a lane.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,925 +10,6 @@ namespace kairos {
 namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid-wide barrier of a cooperative launch (all blocks resident).  Every wait is bounded:
-// past the limit the block records KERR_BARRIER_TIMEOUT and leaves.  Returns true when the
-// launch may go on (no error recorded anywhere).
-__device__ __forceinline__ bool grid_sync(EdgeMapCtr *c, int *s_flag, unsigned long long limit) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned gen = ld_acquire(&c->bar_gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (ld_acquire(&c->bar_gen) == gen) {
-                if (++spins > limit) {
-                    atomicCAS(&c->err, 0, KERR_BARRIER_TIMEOUT);
-                    break;
-                }
-                __nanosleep(128);
-            }
-        }
-        __threadfence();
-        *s_flag = __ldcg(&c->err);
-    }
-    __syncthreads();
-    return *s_flag == 0;
-}
-
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
-// First indices i in [0, deg) with tl[i] >= x and with tl[i] >= y, through the fence keys
-// F (F[k] = tl[32 k]): a binary search over the fences, then one inside a 32-edge block.
-// The two searches are interleaved so that their loads are in flight together.
-__device__ __forceinline__ void lower_bound2_fenced(const uint32_t *__restrict__ tl, uint32_t deg,
-                                                    const uint32_t *__restrict__ F, uint32_t x, uint32_t y,
-                                                    uint32_t &rx, uint32_t &ry) {
-    const uint32_t nf = (deg + FENCE_B - 1) >> FENCE_SHIFT;
-    uint32_t lx = 0, hx = nf, ly = 0, hy = nf;
-    while (lx < hx || ly < hy) {
-        const uint32_t mx = (lx + hx) >> 1, my = (ly + hy) >> 1;
-        const uint32_t fx = lx < hx ? __ldg(&F[mx]) : 0u;
-        const uint32_t fy = ly < hy ? __ldg(&F[my]) : 0u;
-        if (lx < hx) {
-            if (fx < x) lx = mx + 1; else hx = mx;
-        }
-        if (ly < hy) {
-            if (fy < y) ly = my + 1; else hy = my;
-        }
-    }
-    // block b = k - 1 holds the answer in (32 b, min(32 b + 32, deg)]; k == 0 means 0
-    uint32_t bx = lx ? ((lx - 1) << FENCE_SHIFT) + 1 : 0, ex = lx ? min(deg, ((lx - 1) << FENCE_SHIFT) + FENCE_B) : 0;
-    uint32_t by = ly ? ((ly - 1) << FENCE_SHIFT) + 1 : 0, ey = ly ? min(deg, ((ly - 1) << FENCE_SHIFT) + FENCE_B) : 0;
-    while (bx < ex || by < ey) {
-        const uint32_t mx = (bx + ex) >> 1, my = (by + ey) >> 1;
-        const uint32_t tx = bx < ex ? __ldg(&tl[mx]) : 0u;
-        const uint32_t ty = by < ey ? __ldg(&tl[my]) : 0u;
-        if (bx < ex) {
-            if (tx < x) bx = mx + 1; else ex = mx;
-        }
-        if (by < ey) {
-            if (ty < y) by = my + 1; else ey = my;
-        }
-    }
-    rx = bx;
-    ry = by;
-}
-
-template <int W>
-struct WarpSmem {
-    uint32_t thr[32][W];  // per slot and lane: first departure to scan
-    uint32_t lim[32][W];  // per slot and lane: scan below this departure
-    uint32_t act[32];     // per slot: lanes whose interval [thr, lim) is non-empty
-    uint64_t base[32];    // per slot: first edge of its range
-    uint32_t start[32];   // per slot: exclusive prefix of range lengths
-    uint32_t L[32], H[32];
-    uint32_t bthr[W], blim[W];  // lane bounds of the split range being walked
-    // the same bounds as sorted breakpoints: lanes {q : thr_q <= t < lim_q} = bmask[i]
-    // for bkey[i] <= t < bkey[i + 1] (bkey[-1] = -inf, mask 0)
-    uint32_t bkey[2 * W], bmask[2 * W];
-};
-
-// Per-warp phase timer (diagnostics): adds the cycles since the last mark to phase p.
-struct PhaseClock {
-    bool on;
-    long long last;
-    unsigned long long acc[8];
-    __device__ __forceinline__ void init(bool enable) {
-        on = enable;
-        last = on ? clock64() : 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = 0;
-    }
-    __device__ __forceinline__ void mark(int p) {
-        if (on) {
-            const long long now = clock64();
-            acc[p] += (unsigned long long)(now - last);
-            last = now;
-        }
-    }
-};
-
-// Per-thread constants of its query lane q = lane % W.
-struct LaneReg {
-    int q, grp;
-    bool on;
-    uint32_t tw, lim_cap, strict;
-    int32_t src;
-};
-
-struct BlockSmem {
-    uint32_t tw[MAX_LANES];   // window end per lane
-    uint32_t cnt[MAX_LANES];  // relaxations per lane (lanes > 1)
-    int flag;
-};
-
-constexpr int K_EDGES = 4;  // independent edges per thread per step
-
-// Sorted breakpoints of the lane intervals [thr_q, lim_q) of the chunk being walked, and
-// for each breakpoint the lanes whose interval contains it (so that for departure t the
-// candidate lanes are bmask[i] with bkey[i] <= t < bkey[i+1]).  Inactive lanes contribute
-// keys INF.  A bitonic sort of the 2W keys, W <= 32, two per thread.
-template <int W>
-__device__ __forceinline__ void build_breakpoints(WarpSmem<W> &S, int lane, uint32_t act) {
-    constexpr int N = 2 * W;  // keys; thread `lane` holds keys lane and lane + 32 when present
-    uint32_t k0 = INF, k1 = INF;
-    if (lane < W) {
-        const bool on = (act >> lane) & 1u;
-        k0 = on ? S.bthr[lane] : INF;
-        k1 = on ? S.blim[lane] : INF;
-    }
-    // element index e = lane (k0) for e < 32 or lane + 32 (k1); with N <= 32 both live in
-    // k0 of lanes [0, N): rearrange so that element e sits in thread e % 32, slot e / 32
-    uint32_t x0, x1;
-    if constexpr (N <= 32) {
-        // element e: e < W -> thr of lane e, else lim of lane e - W
-        const uint32_t a0 = __shfl_sync(0xFFFFFFFFu, k0, lane % W);
-        const uint32_t a1 = __shfl_sync(0xFFFFFFFFu, k1, lane % W);
-        x0 = lane < W ? a0 : (lane < N ? a1 : INF);
-        x1 = INF;
-    } else {  // W == 32: thread lane holds thr (element lane) and lim (element lane + 32)
-        x0 = k0;
-        x1 = k1;
-    }
-    // bitonic sort of 64 slots (32 threads x 2), ascending by element index lane + 32 * slot
-#pragma unroll
-    for (int size = 2; size <= 64; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride == 32) {  // partners are the two slots of the same thread
-                const bool up = (lane & size) == 0 || size == 64;
-                const uint32_t lo = min(x0, x1), hi = max(x0, x1);
-                x0 = up ? lo : hi;
-                x1 = up ? hi : lo;
-            } else {
-#pragma unroll
-                for (int slot = 0; slot < 2; ++slot) {
-                    uint32_t &x = slot ? x1 : x0;
-                    const int e = lane + 32 * slot;
-                    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, stride);
-                    const bool up = (e & size) == 0;
-                    const bool lower = (e & stride) == 0;
-                    x = (lower == up) ? min(x, y) : max(x, y);
-                }
-            }
-        }
-    }
-    // masks: lanes q with thr_q <= key < lim_q
-    if constexpr (N <= 32) {
-        if (lane < N) {
-            uint32_t m = 0;
-            for (int q = 0; q < W; ++q)
-                if (((act >> q) & 1u) && S.bthr[q] <= x0 && x0 < S.blim[q]) m |= 1u << q;
-            S.bkey[lane] = x0;
-            S.bmask[lane] = m;
-        }
-    } else {
-        uint32_t m0 = 0, m1 = 0;
-        for (int q = 0; q < W; ++q) {
-            if (!((act >> q) & 1u)) continue;
-            const uint32_t th = S.bthr[q], li = S.blim[q];
-            if (th <= x0 && x0 < li) m0 |= 1u << q;
-            if (th <= x1 && x1 < li) m1 |= 1u << q;
-        }
-        S.bkey[lane] = x0;
-        S.bmask[lane] = m0;
-        S.bkey[lane + 32] = x1;
-        S.bmask[lane + 32] = m1;
-    }
-    __syncwarp();
-}
-
-// Append the (up to K_EDGES) vertices this thread marked to the next frontier queue: one
-// warp-wide prefix sum and one atomic per warp.
-__device__ __forceinline__ void frontier_append_k(uint32_t needmask, const int32_t (&d)[K_EDGES], int lane,
-                                                  int32_t *queue, unsigned *count) {
-    const uint32_t c = __popc(needmask);
-    uint32_t incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const uint32_t total = __shfl_sync(FULL, incl, 31);
-    if (total == 0) return;
-    unsigned base = 0;
-    if (lane == 31) base = atomicAdd(count, total);
-    base = __shfl_sync(FULL, base, 31) + incl - c;
-#pragma unroll
-    for (int k = 0; k < K_EDGES; ++k)
-        if ((needmask >> k) & 1u) queue[base++] = d[k];
-}
-
-// Relax K edges per thread (d < 0: none).  Edge k of this thread comes from a slot whose
-// active lanes are act(k) and whose bounds for lane q are bounds(k, q, thr, lim).
-// A lane whose (possibly stale, never too low) copy of the head's label is above the
-// arrival issues a fire-and-forget atomic minimum; the head then gets one frontier-bitmap
-// test-and-set per edge.  A head marked although another thread lowered it first is
-// harmless: its next expansion finds every interval empty.
-template <int W, typename ActF, typename BoundsF>
-__device__ __forceinline__ void relax_k(const EdgeMapArgs &a, const int32_t (&d)[K_EDGES], const uint32_t (&tt)[K_EDGES],
-                                        const uint32_t (&ll)[K_EDGES], ActF actf, BoundsF bounds, BlockSmem &B,
-                                        unsigned long long &cnt1, int lane, int nxt, int n3, uint32_t &hit) {
-    uint32_t mark = 0;  // bit k: edge k lowered its head in some lane
-    if (a.relax_mode == 1) {
-        // every usable edge lowers its head unconditionally (fire-and-forget) and marks it
-        // in the next bitmap (fire-and-forget): no load, no wait, no queue
-#pragma unroll
-        for (int k = 0; k < K_EDGES; ++k) {
-            if (d[k] < 0) continue;
-            const uint32_t tau = tt[k] + ll[k];
-            uint32_t cand = 0;
-            if constexpr (W == 1) {
-                uint32_t th, li;
-                bounds(k, 0, th, li);
-                cand = (actf(k) && th <= tt[k] && tt[k] < li && tau <= B.tw[0]) ? 1u : 0u;
-                cnt1 += cand;
-            } else {
-                uint32_t act = actf(k);
-                while (act) {
-                    const int q = __ffs(act) - 1;
-                    act &= act - 1;
-                    uint32_t th, li;
-                    bounds(k, q, th, li);
-                    if (th <= tt[k] && tt[k] < li && tau <= B.tw[q]) cand |= 1u << q;
-                }
-                if (a.count_relaxed)
-                    for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicAdd(&B.cnt[__ffs(c2) - 1], 1u);
-            }
-            if (cand) {
-                uint32_t *row = a.arr + (size_t)d[k] * W;
-                for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicMin(row + (__ffs(c2) - 1), tau);
-                atomicOr(&a.bm[nxt][d[k] >> 5], 1u << (d[k] & 31));
-                hit |= cand;
-            }
-        }
-        return;
-    }
-    if constexpr (W == 1) {
-        bool ok[K_EDGES];
-        uint32_t cur[K_EDGES];
-#pragma unroll
-        for (int k = 0; k < K_EDGES; ++k) {
-            uint32_t th, li;
-            bounds(k, 0, th, li);
-            ok[k] = d[k] >= 0 && actf(k) && th <= tt[k] && tt[k] < li && tt[k] + ll[k] <= B.tw[0];
-            cnt1 += ok[k];  // a register add: kept even when statistics are not requested
-        }
-#pragma unroll
-        for (int k = 0; k < K_EDGES; ++k) cur[k] = ok[k] ? __ldcg(a.arr + d[k]) : 0u;
-#pragma unroll
-        for (int k = 0; k < K_EDGES; ++k) {
-            const uint32_t tau = tt[k] + ll[k];
-            if (ok[k] && tau < cur[k]) {
-                atomicMin(a.arr + d[k], tau);  // result unused: a reduction
-                mark |= 1u << k;
-                hit = 1u;
-            }
-        }
-    } else {
-        if (a.relax_mode == 2) {
-            // candidate lanes of each edge from the time bounds alone (shared memory)
-            uint32_t cand_k[K_EDGES];
-    #pragma unroll
-            for (int k = 0; k < K_EDGES; ++k) {
-                uint32_t cand = 0;
-                const uint32_t tau = tt[k] + ll[k];
-                if (d[k] >= 0) {
-                    uint32_t act = actf(k);
-                    while (act) {
-                        const int q = __ffs(act) - 1;
-                        act &= act - 1;
-                        uint32_t th, li;
-                        bounds(k, q, th, li);
-                        if (th <= tt[k] && tt[k] < li && tau <= B.tw[q]) cand |= 1u << q;
-                    }
-                    if (a.count_relaxed)
-                        for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicAdd(&B.cnt[__ffs(c2) - 1], 1u);
-                }
-                cand_k[k] = cand;
-            }
-            // the head-row segments holding candidates, one per edge per pass: every edge of the
-            // thread has a segment load in flight at once, and the passes stop when no edge has
-            // candidates left (cost follows the candidates, not the lane width)
-            constexpr int SEGL = (W >= 4) ? 4 : W;
-            uint32_t rem[K_EDGES];
-    #pragma unroll
-            for (int k = 0; k < K_EDGES; ++k) rem[k] = cand_k[k];
-            for (;;) {
-                bool any = false;
-                uint32_t v4[K_EDGES][SEGL];
-                int sgk[K_EDGES];
-    #pragma unroll
-                for (int k = 0; k < K_EDGES; ++k) {
-                    sgk[k] = -1;
-                    if (rem[k]) {
-                        any = true;
-                        const int sg = (__ffs(rem[k]) - 1) / SEGL;
-                        sgk[k] = sg;
-                        const uint32_t *row = a.arr + (size_t)d[k] * W + sg * SEGL;
-                        if constexpr (SEGL == 4) {
-                            const uint4 v = *reinterpret_cast<const uint4 *>(row);  // may be stale: never below
-                            v4[k][0] = v.x;
-                            v4[k][1] = v.y;
-                            v4[k][2] = v.z;
-                            v4[k][3] = v.w;
-                        } else {
-                            const uint2 v = *reinterpret_cast<const uint2 *>(row);
-                            v4[k][0] = v.x;
-                            v4[k][1] = v.y;
-                        }
-                    }
-                }
-                if (!any) break;
-    #pragma unroll
-                for (int k = 0; k < K_EDGES; ++k) {
-                    if (sgk[k] < 0) continue;
-                    const uint32_t tau = tt[k] + ll[k];
-                    uint32_t *row = a.arr + (size_t)d[k] * W + sgk[k] * SEGL;
-    #pragma unroll
-                    for (int j = 0; j < SEGL; ++j) {
-                        const int q = sgk[k] * SEGL + j;
-                        if (((rem[k] >> q) & 1u) && tau < v4[k][j]) {
-                            atomicMin(row + j, tau);  // result unused: a reduction
-                            mark |= 1u << k;
-                            hit |= 1u << q;
-                        }
-                    }
-                    const uint32_t segbits = (SEGL == 32) ? 0xFFFFFFFFu : (((1u << SEGL) - 1u) << (sgk[k] * SEGL));
-                    rem[k] &= ~segbits;
-                }
-            }
-        } else {
-            // candidate lanes of each edge from the time bounds, then the head's state-row
-            // segments holding them, fetched with independent vector loads
-            constexpr int SEG = (W >= 4) ? 4 : W;  // lanes per load
-            constexpr int NSEG = W / SEG;
-            constexpr uint32_t SEGMASK = (SEG == 32) ? 0xFFFFFFFFu : ((1u << SEG) - 1u);
-    #pragma unroll
-            for (int k = 0; k < K_EDGES; ++k) {
-                uint32_t cand = 0;
-                const uint32_t tau = tt[k] + ll[k];
-                if (d[k] >= 0) {
-                    uint32_t act = actf(k);
-                    while (act) {
-                        const int q = __ffs(act) - 1;
-                        act &= act - 1;
-                        uint32_t th, li;
-                        bounds(k, q, th, li);
-                        if (th <= tt[k] && tt[k] < li && tau <= B.tw[q]) cand |= 1u << q;
-                    }
-                    if (a.count_relaxed)
-                        for (uint32_t c2 = cand; c2; c2 &= c2 - 1) atomicAdd(&B.cnt[__ffs(c2) - 1], 1u);
-                }
-                if (cand) {
-                    uint32_t *row = a.arr + (size_t)d[k] * W;
-                    uint32_t cur[W];
-    #pragma unroll
-                    for (int sg = 0; sg < NSEG; ++sg) {
-                        if ((cand >> (sg * SEG)) & SEGMASK) {
-                            if constexpr (SEG == 4) {
-                                const uint4 v = *reinterpret_cast<const uint4 *>(row + sg * 4);  // may be stale: never below
-                                cur[sg * 4] = v.x;
-                                cur[sg * 4 + 1] = v.y;
-                                cur[sg * 4 + 2] = v.z;
-                                cur[sg * 4 + 3] = v.w;
-                            } else {
-                                const uint2 v = *reinterpret_cast<const uint2 *>(row);
-                                cur[0] = v.x;
-                                cur[1] = v.y;
-                            }
-                        } else {
-    #pragma unroll
-                            for (int j = 0; j < SEG; ++j) cur[sg * SEG + j] = 0u;
-                        }
-                    }
-    #pragma unroll
-                    for (int q = 0; q < W; ++q)
-                        if (((cand >> q) & 1u) && tau < cur[q]) {
-                            atomicMin(row + q, tau);  // result unused: a reduction
-                            mark |= 1u << k;
-                            hit |= 1u << q;
-                        }
-                }
-            }
-        }
-    }
-    // one bitmap test-and-set per marked edge, all in flight together
-    uint32_t old[K_EDGES];
-#pragma unroll
-    for (int k = 0; k < K_EDGES; ++k)
-        old[k] = ((mark >> k) & 1u) ? atomicOr(&a.bm[nxt][d[k] >> 5], 1u << (d[k] & 31)) : 0xFFFFFFFFu;
-    uint32_t need = 0;
-#pragma unroll
-    for (int k = 0; k < K_EDGES; ++k)
-        if (!((old[k] >> (d[k] & 31)) & 1u)) need |= 1u << k;
-    frontier_append_k(need, d, lane, a.queue[nxt], &a.ctr->qcount[n3].v);
-}
-
-// Expand up to 32 frontier vertices (one per thread, u < 0 for none).
-template <int W, typename LamT>
-__device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, BlockSmem &B, const LaneReg &R, int lane,
-                                       int32_t u, int nxt, int c3, int n3, unsigned long long &cnt1,
-                                       unsigned long long &scanned, PhaseClock &pc, uint32_t &hit) {
-    const LamT *__restrict__ lam = (const LamT *)a.lam;
-    // 1. lane states of the 32 slots: thread (k, lane) handles slot (32k + lane) / W, lane q
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-        const int j = (k * 32 + lane) / W;
-        const int32_t uj = (W == 1) ? u : __shfl_sync(FULL, u, j);
-        uint32_t th = INF, li = 0;
-        if (uj >= 0 && R.on) {
-            const size_t idx = (size_t)uj * W + R.q;
-            const uint32_t av = __ldcg(&a.arr[idx]);
-            if (av != INF) {
-                const uint32_t pv = __ldcg(&a.prev[idx]);
-                const uint32_t t0 = av + ((R.strict && uj != R.src) ? 1u : 0u);
-                const uint32_t l0 = pv < R.lim_cap ? pv : R.lim_cap;
-                if (t0 < l0) {
-                    th = t0;
-                    li = l0;
-                    __stcg(&a.prev[idx], t0);
-                }
-            }
-        }
-        S.thr[j][R.q] = th;
-        S.lim[j][R.q] = li;
-        const unsigned on = __ballot_sync(FULL, th < li);
-        uint32_t mn = th, mx = li;
-#pragma unroll
-        for (int o = 1; o < W; o <<= 1) {
-            mn = min(mn, __shfl_xor_sync(FULL, mn, o));
-            mx = max(mx, __shfl_xor_sync(FULL, mx, o));
-        }
-        if (R.q == 0) {
-            S.L[j] = mn;
-            S.H[j] = mx;
-            S.act[j] = (W == 32) ? on : ((on >> (lane & ~(W - 1))) & ((1u << W) - 1u));
-        }
-    }
-    __syncwarp();
-    pc.mark(0);
-    // 2. edge range of slot `lane`: [lower_bound(min thr), lower_bound(max lim)) when the
-    // vertex is indexed, its whole list otherwise
-    uint32_t len = 0;
-    uint64_t base = 0;
-    const uint32_t Lm = S.L[lane], Hm = S.H[lane];
-    if (u >= 0 && Lm < Hm) {
-        const uint64_t o0 = __ldg(&a.off[u]);
-        const uint32_t deg = (uint32_t)(__ldg(&a.off[u + 1]) - o0);
-        const uint32_t fi = a.fidx ? __ldg(&a.fidx[u]) : NO_FENCE;
-        uint32_t lo = 0, hi = deg;
-        if (fi != NO_FENCE) lower_bound2_fenced(a.t + o0, deg, a.fence + fi, Lm, Hm, lo, hi);
-        len = hi - lo;
-        base = o0 + lo;
-    }
-    pc.mark(1);
-    // 3. ranges longer than warp_max_edges go to the grid-wide chunk list (one pair of
-    // atomics per warp)
-    const bool isbig = len > (uint32_t)a.warp_max_edges;
-    const unsigned bmask = __ballot_sync(FULL, isbig);
-    if (bmask) {
-        const uint32_t CH = (uint32_t)a.chunk_edges;
-        const uint32_t nch = isbig ? (len + CH - 1) / CH : 0u;
-        const uint32_t chincl = warp_incl_scan(nch, lane);
-        const uint32_t chtot = __shfl_sync(FULL, chincl, 31);
-        unsigned e0 = 0, c0 = 0;
-        if (lane == 0) {
-            e0 = atomicAdd(&a.ctr->bigcount[c3].v, (unsigned)__popc(bmask));
-            c0 = atomicAdd(&a.ctr->chunks[c3].v, chtot);
-        }
-        e0 = __shfl_sync(FULL, e0, 0);
-        c0 = __shfl_sync(FULL, c0, 0);
-        if (isbig) {
-            const uint32_t e = e0 + __popc(bmask & ((1u << lane) - 1u));
-            const uint32_t cb = c0 + chincl - nch;
-            if (e < a.cap_big && (uint64_t)cb + nch <= a.cap_chunks) {
-                BigEntry be;
-                be.base = base;
-                be.len = len;
-                be.chunk_base = cb;
-                be.act = S.act[lane];
-                be.pad = 0;
-                a.big[e] = be;
-                for (int qq = 0; qq < W; ++qq) {
-                    a.bigb[((size_t)e * W + qq) * 2] = S.thr[lane][qq];
-                    a.bigb[((size_t)e * W + qq) * 2 + 1] = S.lim[lane][qq];
-                }
-                __threadfence();  // the entry is visible before any chunk names it
-                for (uint32_t c = 0; c < nch; ++c) st_release(&a.chunk_owner[cb + c], e);
-            } else {
-                atomicCAS(&a.ctr->err, 0, KERR_CAPACITY);
-            }
-            len = 0;
-        }
-    }
-    pc.mark(2);
-    // 4. walk the concatenated short ranges, K_EDGES x 32 edges per step
-    const uint32_t incl = warp_incl_scan(len, lane);
-    const uint32_t T = __shfl_sync(FULL, incl, 31);
-    S.start[lane] = incl - len;
-    S.base[lane] = base;
-    __syncwarp();
-    for (uint32_t c = 0; c < T; c += 32 * K_EDGES) {
-        int32_t d[K_EDGES];
-        uint32_t tt[K_EDGES], ll[K_EDGES];
-        int sl[K_EDGES];
-#pragma unroll
-        for (int k = 0; k < K_EDGES; ++k) {
-            const uint32_t item = c + k * 32 + lane;
-            d[k] = -1;
-            tt[k] = 0;
-            ll[k] = 0;
-            sl[k] = 0;
-            if (item < T) {
-                int j = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1)
-                    if (S.start[j + step] <= item) j += step;
-                sl[k] = j;
-                const uint64_t e = S.base[j] + (item - S.start[j]);
-                d[k] = __ldg(&a.dst[e]);
-                tt[k] = __ldg(&a.t[e]);
-                ll[k] = (uint32_t)__ldg(&lam[e]);
-                ++scanned;
-            }
-        }
-        relax_k<W>(a, d, tt, ll, [&](int k) { return S.act[sl[k]]; },
-                   [&](int k, int q, uint32_t &th, uint32_t &li) {
-                       th = S.thr[sl[k]][q];
-                       li = S.lim[sl[k]][q];
-                   },
-                   B, cnt1, lane, nxt, n3, hit);
-    }
-    __syncwarp();
-    pc.mark(3);
-}
-
-template <int W, typename LamT>
-__global__ void __launch_bounds__(EM_THREADS, (W == 1 ? 4 : (W == 32 ? 2 : 3))) edgemap_kernel(const EdgeMapArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ BlockSmem B;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    WarpSmem<W> &S = reinterpret_cast<WarpSmem<W> *>(smem_raw)[wib];
-    const size_t tid = (size_t)blockIdx.x * EM_THREADS + threadIdx.x;
-    const size_t nthr = (size_t)gridDim.x * EM_THREADS;
-    const int64_t n = a.n;
-    const size_t nwords = (size_t)((n + 31) >> 5);
-    EdgeMapCtr *C = a.ctr;
-    const LamT *__restrict__ lam = (const LamT *)a.lam;
-
-    LaneReg R;
-    R.q = lane % W;
-    R.grp = lane / W;
-    R.on = R.q < a.lanes.nlanes && ((a.running_mask >> R.q) & 1u);
-    R.tw = a.lanes.tw[R.q];
-    R.lim_cap = R.tw + 1u;
-    R.strict = (a.lanes.strict_mask >> R.q) & 1u;
-    R.src = a.lanes.src[R.q];
-    if (threadIdx.x < MAX_LANES) {
-        B.tw[threadIdx.x] = a.lanes.tw[threadIdx.x];
-        B.cnt[threadIdx.x] = 0;
-    }
-    unsigned long long cnt1 = 0, scanned = 0;
-    unsigned reached = 0;
-    PhaseClock pc;
-    pc.init(a.phase_clock != 0);
-
-    // ---- initial labels (Alg. 2: t[x] = window start, t[v] = infinity) ----
-    if (!a.resume) {
-    for (size_t i = tid; i < (size_t)n * W; i += nthr) {
-        a.arr[i] = INF;
-        a.prev[i] = INF;
-    }
-    for (size_t i = tid; i < nwords; i += nthr) {
-        a.bm[0][i] = 0u;
-        a.bm[1][i] = 0u;
-    }
-    if (!grid_sync(C, &B.flag, a.spin_limit)) return;
-    if (blockIdx.x == 0 && threadIdx.x < (unsigned)a.lanes.nlanes && ((a.running_mask >> threadIdx.x) & 1u)) {
-        const int qq = threadIdx.x;
-        const int32_t s = a.lanes.src[qq];
-        a.arr[(size_t)s * W + qq] = a.lanes.ta[qq];
-        const uint32_t bit = 1u << (s & 31);
-        const uint32_t old = atomicOr(&a.bm[0][s >> 5], bit);
-        if (!(old & bit)) a.queue[0][atomicAdd(&C->qcount[0].v, 1u)] = s;
-    }
-    if (!grid_sync(C, &B.flag, a.spin_limit)) return;
-    }
-
-    // ---- rounds ----
-    unsigned r = a.round_begin;
-    for (; r < a.round_end; ++r) {
-        uint32_t hit = 0;  // lanes this thread lowered a label in, this round
-        const int cur = r & 1, nxt = cur ^ 1;
-        const int c3 = r % 3, n3 = (r + 1) % 3, p3 = (r + 2) % 3;
-        // relax_mode 1 keeps no queue: after round 0 the bitmap is the frontier, and a round
-        // without usable edges in any lane (active mask 0) ends the launch
-        const unsigned F = (a.relax_mode == 1 && r > 0) ? (__ldcg(&C->active[p3].v) ? 1u : 0u)
-                                                        : __ldcg(&C->qcount[c3].v);
-        if (tid == 0 && r <= PROFILE_ROUNDS) {
-            C->round_ns[r] = globaltimer();
-            if (r > 0) C->round_chunks[r - 1] = __ldcg(&C->chunks[(r + 2) % 3].v);
-            if (r < PROFILE_ROUNDS) C->round_frontier[r] = F;
-        }
-        if (F == 0) break;
-        if (r >= a.max_rounds) {
-            if (tid == 0) atomicCAS(&C->err, 0, KERR_ROUNDS);
-            break;
-        }
-        if (tid == 0) {
-            C->qcount[p3].v = 0;
-            C->bigcount[n3].v = 0;
-            C->chunks[n3].v = 0;
-            C->chunk_next[n3].v = 0;
-            C->bnext[n3].v = 0;
-            C->bdone[n3].v = 0;
-            C->active[n3].v = 0;
-        }
-        const bool dense = a.relax_mode == 1 || (a.dense_div > 0 && (int64_t)F * a.dense_div > n);
-        // work of the round: batches of 32 queued vertices (or 1024-vertex bitmap stripes),
-        // then the chunks that expanding them registered; both claimed dynamically
-        const unsigned nb = dense ? (unsigned)((nwords + 31) / 32) : (F + 31) / 32;
-        for (;;) {
-            unsigned b = nb;
-            if (lane == 0 && __ldcg(&C->bnext[c3].v) < nb) b = atomicAdd(&C->bnext[c3].v, 1u);
-            b = __shfl_sync(FULL, b, 0);
-            if (b < nb) {
-                if (!dense) {
-                    const unsigned i = b * 32 + lane;
-                    const int32_t u = (i < F) ? __ldcg(&a.queue[cur][i]) : -1;
-                    if (u >= 0) atomicAnd(&a.bm[cur][u >> 5], ~(1u << (u & 31)));
-                    expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned, pc, hit);
-                } else {
-                    // ballot-compact the 1024-vertex stripe, 32 vertices at a time
-                    const size_t wb = (size_t)b * 32;
-                    const size_t w = wb + lane;
-                    const uint32_t bits = (w < nwords) ? __ldcg(&a.bm[cur][w]) : 0u;
-                    if (bits) a.bm[cur][w] = 0u;
-                    const uint32_t cnt = __popc(bits);
-                    const uint32_t incl = warp_incl_scan(cnt, lane);
-                    const uint32_t pre = incl - cnt;
-                    const uint32_t total = __shfl_sync(FULL, incl, 31);
-                    for (uint32_t b2 = 0; b2 < total; b2 += 32) {
-                        const uint32_t k = b2 + lane;
-                        int j = 0;
-#pragma unroll
-                        for (int step = 16; step >= 1; step >>= 1) {
-                            const uint32_t pj = __shfl_sync(FULL, pre, j + step);
-                            if (pj <= k) j += step;
-                        }
-                        const uint32_t bj = __shfl_sync(FULL, bits, j);
-                        const uint32_t pj = __shfl_sync(FULL, pre, j);
-                        int32_t u = -1;
-                        if (k < total) u = (int32_t)((wb + j) * 32 + __fns(bj, 0, (int)(k - pj) + 1));
-                        expand<W, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned, pc, hit);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence();  // chunk registrations of this batch precede its completion
-                    atomicAdd(&C->bdone[c3].v, 1u);
-                }
-                continue;
-            }
-            // all batches are claimed: take the next chunk id, waiting (bounded) until it is
-            // published, or until every batch is done and no chunk has that id
-            unsigned c = 0, e = NO_OWNER;
-            int state = 0;  // 0 wait, 1 work, 2 no more work
-            if (lane == 0) {
-                // no claim while every registered chunk is taken and no batch can add more
-                unsigned backoff = 32;
-                unsigned long long spins = 0;
-                for (;;) {
-                    const unsigned have = __ldcg(&C->chunks[c3].v);
-                    if (__ldcg(&C->chunk_next[c3].v) < have) break;
-                    if (ld_acquire(&C->bdone[c3].v) >= nb && __ldcg(&C->chunk_next[c3].v) >= __ldcg(&C->chunks[c3].v)) {
-                        state = 2;
-                        break;
-                    }
-                    if (__ldcg(&C->err) != 0 || ++spins > a.spin_limit) {
-                        if (spins > a.spin_limit) atomicCAS(&C->err, 0, KERR_WAIT_TIMEOUT);
-                        state = 2;
-                        break;
-                    }
-                    __nanosleep(backoff);
-                    backoff = backoff < 1024 ? 2 * backoff : 1024;
-                }
-                if (state == 0) c = atomicAdd(&C->chunk_next[c3].v, 1u);
-                while (state == 0) {
-                    if (c < __ldcg(&C->chunks[c3].v) && c < a.cap_chunks) {
-                        e = ld_acquire(&a.chunk_owner[c]);
-                        if (e != NO_OWNER) {
-                            state = 1;
-                            break;
-                        }
-                    } else if (ld_acquire(&C->bdone[c3].v) >= nb && c >= __ldcg(&C->chunks[c3].v)) {
-                        state = 2;
-                        break;
-                    }
-                    if (__ldcg(&C->err) != 0) {
-                        state = 2;
-                        break;
-                    }
-                    if (++spins > a.spin_limit) {
-                        atomicCAS(&C->err, 0, KERR_WAIT_TIMEOUT);
-                        state = 2;
-                        break;
-                    }
-                    __nanosleep(backoff);
-                    backoff = backoff < 1024 ? 2 * backoff : 1024;
-                }
-            }
-            state = __shfl_sync(FULL, state, 0);
-            pc.mark(4);
-            if (state == 2) break;
-            c = __shfl_sync(FULL, c, 0);
-            e = __shfl_sync(FULL, e, 0);
-            if (lane == 0) a.chunk_owner[c] = NO_OWNER;  // free the id for the next round
-            if (e >= a.cap_big) continue;
-            const uint64_t bbase = __ldcg((const unsigned long long *)&a.big[e].base);
-            const uint32_t blen = __ldcg(&a.big[e].len);
-            const uint32_t bcb = __ldcg(&a.big[e].chunk_base);
-            const uint32_t bact = __ldcg(&a.big[e].act);
-            if (c < bcb) continue;
-            const uint32_t st = (c - bcb) * (uint32_t)a.chunk_edges;
-            if (st >= blen) continue;
-            const uint32_t cnt = min((uint32_t)a.chunk_edges, blen - st);
-            if (lane < W) {
-                S.bthr[lane] = __ldcg(&a.bigb[((size_t)e * W + lane) * 2]);
-                S.blim[lane] = __ldcg(&a.bigb[((size_t)e * W + lane) * 2 + 1]);
-            }
-            __syncwarp();
-            if (W > 1) build_breakpoints<W>(S, lane, bact);
-            for (uint32_t i = 0; i < cnt; i += 32 * K_EDGES) {
-                int32_t d[K_EDGES];
-                uint32_t tt[K_EDGES], ll[K_EDGES];
-#pragma unroll
-                for (int k = 0; k < K_EDGES; ++k) {
-                    const uint32_t item = i + k * 32 + lane;
-                    d[k] = -1;
-                    tt[k] = 0;
-                    ll[k] = 0;
-                    if (item < cnt) {
-                        const uint64_t ed = bbase + st + item;
-                        d[k] = __ldg(&a.dst[ed]);
-                        tt[k] = __ldg(&a.t[ed]);
-                        ll[k] = (uint32_t)__ldg(&lam[ed]);
-                        ++scanned;
-                    }
-                }
-                relax_k<W>(a, d, tt, ll,
-                           [&](int k) -> uint32_t {
-                               if (W == 1) return bact;
-                               int lo = 0, hi = 2 * W;  // first breakpoint above t
-                               while (lo < hi) {
-                                   const int mid = (lo + hi) >> 1;
-                                   if (S.bkey[mid] <= tt[k]) lo = mid + 1; else hi = mid;
-                               }
-                               return lo ? S.bmask[lo - 1] : 0u;
-                           },
-                           [&](int, int q, uint32_t &th, uint32_t &li) {
-                               if (W == 1) {
-                                   th = S.bthr[q];
-                                   li = S.blim[q];
-                               } else {  // the mask already holds exactly the lanes whose interval contains t
-                                   th = 0u;
-                                   li = INF;
-                               }
-                           },
-                           B, cnt1, lane, nxt, n3, hit);
-            }
-            __syncwarp();
-            pc.mark(5);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) hit |= __shfl_xor_sync(FULL, hit, o);
-        if (lane == 0 && hit) atomicOr(&C->active[c3].v, hit);
-        pc.mark(7);
-        if (!grid_sync(C, &B.flag, a.spin_limit)) return;
-        pc.mark(6);
-        if (tid == 0) C->last_active = __ldcg(&C->active[c3].v);
-    }
-
-    // ---- read out: out[row_q][v] = label (mirrored back for latest departure) ----
-    for (size_t i = tid; !a.resume && i < (size_t)n * W; i += nthr) {
-        // nthr is a multiple of W, so this thread always sees lane R.q
-        if (!R.on) continue;
-        const size_t v = i / W;
-        const uint32_t x = __ldcg(&a.arr[i]);
-        reached += (x != INF);
-        if (a.out) {
-            const bool mir = (a.lanes.mirror_mask >> R.q) & 1u;
-            const uint32_t y = (mir && x != INF) ? TMAX - x : x;
-            if (!(a.out_is_arr && !mir)) a.out[a.lanes.row[R.q] * a.out_stride + (int64_t)v] = y;
-        }
-    }
-    // ---- counters ----
-#pragma unroll
-    for (int o = W; o < 32; o <<= 1) reached += __shfl_xor_sync(FULL, reached, o);
-    unsigned long long sc = scanned;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        sc += __shfl_xor_sync(FULL, sc, o);
-        cnt1 += __shfl_xor_sync(FULL, cnt1, o);
-    }
-    if (lane < W && R.on) atomicAdd(&C->reached[lane], reached);
-    if (lane == 0) atomicAdd(&C->scanned, sc);
-    if (W == 1) {
-        if (lane == 0) atomicAdd(&C->relaxed[0], cnt1);
-    } else {
-        __syncthreads();
-        if (threadIdx.x < (unsigned)W && B.cnt[threadIdx.x])
-            atomicAdd(&C->relaxed[threadIdx.x], (unsigned long long)B.cnt[threadIdx.x]);
-    }
-    if (tid == 0) C->rounds = r;
-    pc.mark(7);
-    if (pc.on && lane == 0)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) atomicAdd(&C->phase_cycles[i], pc.acc[i]);
-}
-
-template <int W, typename LamT>
-cudaError_t launch_t(const EdgeMapArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = sizeof(WarpSmem<W>) * (EM_THREADS / 32);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(edgemap_kernel<W, LamT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    void *args[] = {(void *)&a};
-    return cudaLaunchCooperativeKernel((void *)edgemap_kernel<W, LamT>, dim3(grid), dim3(EM_THREADS), args, smem, s);
-}
-
-template <int W, typename LamT>
-int max_blocks_t() {
-    const size_t smem = sizeof(WarpSmem<W>) * (EM_THREADS / 32);
-    if (cudaFuncSetAttribute(edgemap_kernel<W, LamT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, edgemap_kernel<W, LamT>, EM_THREADS, smem) != cudaSuccess)
-        return 0;
-    return nb;
-}
-
-template <typename LamT>
-cudaError_t launch_l(const EdgeMapArgs &a, int lanes, int grid, cudaStream_t s) {
-    switch (lanes) {
-        case 1: return launch_t<1, LamT>(a, grid, s);
-        case 2: return launch_t<2, LamT>(a, grid, s);
-        case 4: return launch_t<4, LamT>(a, grid, s);
-        case 8: return launch_t<8, LamT>(a, grid, s);
-        case 16: return launch_t<16, LamT>(a, grid, s);
-        case 32: return launch_t<32, LamT>(a, grid, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename LamT>
-int max_blocks_l(int lanes) {
-    switch (lanes) {
-        case 1: return max_blocks_t<1, LamT>();
-        case 2: return max_blocks_t<2, LamT>();
-        case 4: return max_blocks_t<4, LamT>();
-        case 8: return max_blocks_t<8, LamT>();
-        case 16: return max_blocks_t<16, LamT>();
-        case 32: return max_blocks_t<32, LamT>();
-        default: return 0;
-    }
-}
 
 // One warp per 32 vertices and lane (the lane loop is uniform); per-lane sums gather in
 // shared memory and leave with one atomic per block.
@@ -1030,14 +85,31 @@ cudaError_t seed_lane(const EdgeMapArgs &a, int W, int q, int32_t src, uint32_t 
 }
 
 cudaError_t edgemap_launch(const EdgeMapArgs &a, int lanes, int lam_bits, int grid, cudaStream_t s) {
-    return lam_bits == 16 ? launch_l<uint16_t>(a, lanes, grid, s) : launch_l<uint32_t>(a, lanes, grid, s);
+    switch (lanes) {
+        case 1: return edgemap_launch_w<1>(a, lam_bits, grid, s);
+        case 2: return edgemap_launch_w<2>(a, lam_bits, grid, s);
+        case 4: return edgemap_launch_w<4>(a, lam_bits, grid, s);
+        case 8: return edgemap_launch_w<8>(a, lam_bits, grid, s);
+        case 16: return edgemap_launch_w<16>(a, lam_bits, grid, s);
+        case 32: return edgemap_launch_w<32>(a, lam_bits, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
-int edgemap_max_grid(int lanes, int lam_bits, int *blocks_per_sm_out) {
+int edgemap_max_grid(int lanes, int lam_bits, int relax_mode, int *blocks_per_sm_out) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    int nb = lam_bits == 16 ? max_blocks_l<uint16_t>(lanes) : max_blocks_l<uint32_t>(lanes);
+    int nb = 0;
+    switch (lanes) {
+        case 1: nb = edgemap_max_blocks_w<1>(lam_bits, relax_mode); break;
+        case 2: nb = edgemap_max_blocks_w<2>(lam_bits, relax_mode); break;
+        case 4: nb = edgemap_max_blocks_w<4>(lam_bits, relax_mode); break;
+        case 8: nb = edgemap_max_blocks_w<8>(lam_bits, relax_mode); break;
+        case 16: nb = edgemap_max_blocks_w<16>(lam_bits, relax_mode); break;
+        case 32: nb = edgemap_max_blocks_w<32>(lam_bits, relax_mode); break;
+        default: return 0;
+    }
     if (blocks_per_sm_out) *blocks_per_sm_out = nb;
     return nb * sms;
 }

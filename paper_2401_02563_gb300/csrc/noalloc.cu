@@ -159,7 +159,7 @@ extern "C" kairos_status kairos_earliest_arrival_noalloc(kairos_graph *g, int32_
     a.running_mask = 0xFFFFFFFFu;
     a.spin_limit = DEFAULT_SPIN_LIMIT;
     int bps = 0;
-    int grid = edgemap_max_grid(1, g->lam_bits, &bps);
+    int grid = edgemap_max_grid(1, g->lam_bits, 0, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "no-allocation query: no resident launch shape");
     if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
     KAIROS_CUDA(edgemap_launch(a, 1, g->lam_bits, grid, s), "no-allocation query: edge-map launch");

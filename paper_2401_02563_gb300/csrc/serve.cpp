@@ -233,7 +233,7 @@ kairos_status step_session(kairos_server *V, Session &S, std::vector<std::pair<u
     a.round_begin = S.r;
     a.round_end = S.r + (uint32_t)V->slice;
     int bps = 0;
-    int grid = edgemap_max_grid(S.W, g->lam_bits, &bps);
+    int grid = edgemap_max_grid(S.W, g->lam_bits, a.relax_mode, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "serve: no resident launch shape");
     if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
     const auto t_launch = clk::now();
