@@ -94,39 +94,67 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
     return x;
 }
 
-// First indices i in [0, deg) with tl[i] >= x and with tl[i] >= y, through the fence keys
-// F (F[k] = tl[32 k]): a binary search over the fences, then one inside a 32-edge block.
-// The two searches are interleaved so that their loads are in flight together.
+// Lower bounds of two keys in one sorted array, 8-ary: each step loads 7 pivots per key (all
+// in flight together) and keeps the eighth of the range that holds the answer, so a chain of
+// about log8(n) dependent loads replaces log2(n).  On entry and throughout, the answer for x
+// lies in [lx, hx]: A[i] < x for i < lx, and hx is the end or A[hx] >= x (same for y).  On
+// return lx (ly) is the first index with A[i] >= x (y), or the end.
+__device__ __forceinline__ void lower_bound2_kary(const uint32_t *__restrict__ A, uint32_t &lx, uint32_t hx, uint32_t x,
+                                                  uint32_t &ly, uint32_t hy, uint32_t y) {
+    while (hx - lx > 8 || hy - ly > 8) {
+        const uint32_t nx = hx - lx, ny = hy - ly;
+        const bool ax = nx > 8, ay = ny > 8;
+        uint32_t cx = 0, cy = 0;
+        uint32_t vx[7], vy[7];
+#pragma unroll
+        for (int j = 1; j < 8; ++j) {
+            vx[j - 1] = ax ? __ldg(&A[lx + (uint32_t)(((uint64_t)nx * j) >> 3)]) : 0u;
+            vy[j - 1] = ay ? __ldg(&A[ly + (uint32_t)(((uint64_t)ny * j) >> 3)]) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            cx += vx[j] < x;
+            cy += vy[j] < y;
+        }
+        if (ax) {
+            // pivots below x form a prefix: the answer is past pivot cx and at most pivot cx + 1
+            const uint32_t l2 = cx ? lx + (uint32_t)(((uint64_t)nx * cx) >> 3) + 1u : lx;
+            if (cx < 7) hx = lx + (uint32_t)(((uint64_t)nx * (cx + 1)) >> 3);
+            lx = l2;
+        }
+        if (ay) {
+            const uint32_t l2 = cy ? ly + (uint32_t)(((uint64_t)ny * cy) >> 3) + 1u : ly;
+            if (cy < 7) hy = ly + (uint32_t)(((uint64_t)ny * (cy + 1)) >> 3);
+            ly = l2;
+        }
+    }
+    // at most 8 candidates per key: the answer is lx plus the count of those below x
+    uint32_t cx = 0, cy = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool inx = lx + j < hx, iny = ly + j < hy;
+        const uint32_t a = inx ? __ldg(&A[lx + j]) : 0u;
+        const uint32_t b = iny ? __ldg(&A[ly + j]) : 0u;
+        cx += (inx && a < x);
+        cy += (iny && b < y);
+    }
+    lx += cx;
+    ly += cy;
+}
+
+// First indices i in [0, deg) with tl[i] >= x and with tl[i] >= y (deg if none), through the
+// fence keys F (F[k] = tl[32 k]): the fences first, then one 32-edge block.
 __device__ __forceinline__ void lower_bound2_fenced(const uint32_t *__restrict__ tl, uint32_t deg,
                                                     const uint32_t *__restrict__ F, uint32_t x, uint32_t y,
                                                     uint32_t &rx, uint32_t &ry) {
     const uint32_t nf = (deg + FENCE_B - 1) >> FENCE_SHIFT;
-    uint32_t lx = 0, hx = nf, ly = 0, hy = nf;
-    while (lx < hx || ly < hy) {
-        const uint32_t mx = (lx + hx) >> 1, my = (ly + hy) >> 1;
-        const uint32_t fx = lx < hx ? __ldg(&F[mx]) : 0u;
-        const uint32_t fy = ly < hy ? __ldg(&F[my]) : 0u;
-        if (lx < hx) {
-            if (fx < x) lx = mx + 1; else hx = mx;
-        }
-        if (ly < hy) {
-            if (fy < y) ly = my + 1; else hy = my;
-        }
-    }
-    // block b = k - 1 holds the answer in (32 b, min(32 b + 32, deg)]; k == 0 means 0
+    uint32_t lx = 0, ly = 0;
+    lower_bound2_kary(F, lx, nf, x, ly, nf, y);
+    // fence k = lx is the first at or above x: the answer lies in (32 (k - 1), min(32 k, deg)]
+    // (k == 0: it is 0, the first edge)
     uint32_t bx = lx ? ((lx - 1) << FENCE_SHIFT) + 1 : 0, ex = lx ? min(deg, ((lx - 1) << FENCE_SHIFT) + FENCE_B) : 0;
     uint32_t by = ly ? ((ly - 1) << FENCE_SHIFT) + 1 : 0, ey = ly ? min(deg, ((ly - 1) << FENCE_SHIFT) + FENCE_B) : 0;
-    while (bx < ex || by < ey) {
-        const uint32_t mx = (bx + ex) >> 1, my = (by + ey) >> 1;
-        const uint32_t tx = bx < ex ? __ldg(&tl[mx]) : 0u;
-        const uint32_t ty = by < ey ? __ldg(&tl[my]) : 0u;
-        if (bx < ex) {
-            if (tx < x) bx = mx + 1; else ex = mx;
-        }
-        if (by < ey) {
-            if (ty < y) by = my + 1; else ey = my;
-        }
-    }
+    lower_bound2_kary(tl, bx, ex, x, by, ey, y);
     rx = bx;
     ry = by;
 }
@@ -718,17 +746,22 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 || W == 16) ? 4 : (W == 32
             C->active[n3].v = 0;
         }
         const bool dense = MODE == 1 || (a.dense_div > 0 && (int64_t)F * a.dense_div > n);
-        // work of the round: batches of 32 queued vertices (or 1024-vertex bitmap stripes),
-        // then the chunks that expanding them registered; both claimed dynamically
-        const unsigned nb = dense ? (unsigned)((nwords + 31) / 32) : (F + 31) / 32;
+        // work of the round: batches of up to 32 queued vertices (or 1024-vertex bitmap
+        // stripes), then the chunks that expanding them registered; both claimed dynamically.
+        // A small frontier is spread thin (bs vertices per batch, about one batch per warp),
+        // so that no warp walks many short ranges one after another while the others wait.
+        const unsigned nwarps = gridDim.x * (EM_THREADS / 32);
+        const unsigned per = (F + nwarps - 1) / nwarps;
+        const unsigned bs = per >= 32 ? 32u : (per < 1 ? 1u : per);
+        const unsigned nb = dense ? (unsigned)((nwords + 31) / 32) : (F + bs - 1) / bs;
         for (;;) {
             unsigned b = nb;
             if (lane == 0 && __ldcg(&C->bnext[c3].v) < nb) b = atomicAdd(&C->bnext[c3].v, 1u);
             b = __shfl_sync(FULL, b, 0);
             if (b < nb) {
                 if (!dense) {
-                    const unsigned i = b * 32 + lane;
-                    const int32_t u = (i < F) ? __ldcg(&a.queue[cur][i]) : -1;
+                    const unsigned i = b * bs + lane;
+                    const int32_t u = ((unsigned)lane < bs && i < F) ? __ldcg(&a.queue[cur][i]) : -1;
                     if (u >= 0) atomicAnd(&a.bm[cur][u >> 5], ~(1u << (u & 31)));
                     expand<W, MODE, LamT>(a, S, B, R, lane, u, nxt, c3, n3, cnt1, scanned, pc, hit);
                 } else {
@@ -769,7 +802,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 || W == 16) ? 4 : (W == 32
             int state = 0;  // 0 wait, 1 work, 2 no more work
             if (lane == 0) {
                 // no claim while every registered chunk is taken and no batch can add more
-                unsigned backoff = 32;
+                unsigned backoff = 64;
                 unsigned long long spins = 0;
                 for (;;) {
                     const unsigned have = __ldcg(&C->chunks[c3].v);
@@ -784,7 +817,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 || W == 16) ? 4 : (W == 32
                         break;
                     }
                     __nanosleep(backoff);
-                    backoff = backoff < 1024 ? 2 * backoff : 1024;
+                    backoff = backoff < 4096 ? 2 * backoff : 4096;
                 }
                 if (state == 0) c = atomicAdd(&C->chunk_next[c3].v, 1u);
                 while (state == 0) {
@@ -808,7 +841,7 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 || W == 16) ? 4 : (W == 32
                         break;
                     }
                     __nanosleep(backoff);
-                    backoff = backoff < 1024 ? 2 * backoff : 1024;
+                    backoff = backoff < 4096 ? 2 * backoff : 4096;
                 }
             }
             state = __shfl_sync(FULL, state, 0);
