@@ -50,6 +50,23 @@ def parse():
     return p.parse_args()
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per edge-map launch, averaged
+# over the 8 launches of one timed step, from one ncu capture of that step (the command and
+# the per-launch figures are in profiles/).  Keyed by workload, lane width, relaxation mode
+# and a hash of the kernel sources: any change to the kernel voids the figure (null).
+MEASURED_TRAFFIC = {}
+KERNEL_SOURCES = ("paper_2401_02563_gb300/csrc/edgemap_kernel.cuh", "paper_2401_02563_gb300/csrc/common.cuh")
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -460,7 +477,8 @@ def main():
         "index_threshold_sweep": theta_sweep,
         "batched_vs_single_qps": (Q / (step_ms / 1e3)) / single["queries_per_s"] if single else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": "edgemap_kernel",
+                     "traffic": MEASURED_TRAFFIC.get((args.workload, lanes, tuning.relax_mode, kernel_hash())),
+                     "peak_kind": peak_kind, "kernel": "edgemap_kernel", "kernel_hash": kernel_hash(),
                      "launches_per_step": n_launch, "avg_launch_ms": launch_ms,
                      "algorithmic_bytes_per_step": bytes_step},
         "served": served,
