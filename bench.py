@@ -271,20 +271,24 @@ def cpu_baseline(el, queries, budget_s=20.0):
     te = 0
     scan_s = 0.0
     done = []
-    order = []
-    half = len(queries) // 2
-    for k in range(half):  # alternate kinds: EA k, LD k
-        order += [k, half + k]
-    for i in order:
-        t1 = time.perf_counter()
-        lab = orc.query(queries[i])
-        scan_s += time.perf_counter() - t1
-        te += orc.admissible(queries[i], lab)
-        done.append(i)
-        if scan_s > budget_s:
+    # alternate the kinds (EA, LD, EA, ...) through the set; a set that finishes in well under
+    # a second (the tiny workload) is repeated until a second has been timed
+    ea = [i for i, q in enumerate(queries) if q.kind == 0]
+    ld = [i for i, q in enumerate(queries) if q.kind == 1]
+    order = [i for pair in zip(ea, ld) for i in pair] + ea[len(ld):] + ld[len(ea):]
+    while True:
+        for i in order:
+            t1 = time.perf_counter()
+            lab = orc.query(queries[i])
+            scan_s += time.perf_counter() - t1
+            te += orc.admissible(queries[i], lab)
+            done.append(i)
+            if scan_s > budget_s:
+                break
+        if scan_s > min(budget_s, 1.0):
             break
     return {"value": te / scan_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(done)} of {len(queries)} queries ({sum(queries[i].kind == 0 for i in done)} EA, "
+            "sample": f"{len(done)} runs over {len(queries)} queries ({sum(queries[i].kind == 0 for i in done)} EA, "
                       f"{sum(queries[i].kind == 1 for i in done)} LD), one-pass scans on 1 host core; "
                       f"time-order sort ({sort_s:.1f} s) excluded as preprocessing",
             "queries_per_s": len(done) / scan_s}
@@ -321,7 +325,7 @@ def reference_arm(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"{w.name}: {w.description}", "queries_per_step": len(per_step),
-                       "l2": "graph (0.8 GB) larger than L2"},
+                       "l2": "host run (no device caches)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{len(per_step)} queries (1 EA + 1 LD) per step, single-threaded "
                                        f"one-pass scans; time-order sort excluded"},
