@@ -174,9 +174,9 @@ EdgeMapArgs session_args(kairos_graph *g, Session &S) {
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;
     a.count_relaxed = 1;
-    // resumable slices keep the queue frontier; served mixes have few active lanes per
-    // vertex, so only the state segments holding candidate lanes are read
-    a.relax_mode = 2;
+    // resumable slices keep the queue frontier, so the bitmap-frontier mode (1) is replaced
+    // by the all-segment mode (0); otherwise the graph's tuned mode applies
+    a.relax_mode = g->tuning.relax_mode == 1 ? 0 : g->tuning.relax_mode;
     a.running_mask = S.running;
     return a;
 }
