@@ -39,6 +39,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", type=int, default=2)
     p.add_argument("--lanes", type=int, default=0, help="0: autotune")
+    p.add_argument("--shape", default="", help="lanes,warp_max_edges,chunk_edges,dense_div,relax_mode,blocks_per_sm "
+                                               "(fixes the whole launch shape; no autotuning)")
     p.add_argument("--no-single", action="store_true", help="skip the one-query-per-launch comparison")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -51,10 +53,15 @@ def parse():
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per edge-map launch, averaged
-# over the 8 launches of one timed step, from one ncu capture of that step (the command and
-# the per-launch figures are in profiles/).  Keyed by workload, lane width, relaxation mode
-# and a hash of the kernel sources: any change to the kernel voids the figure (null).
-MEASURED_TRAFFIC = {}
+# over the 8 launches of one timed step, from one ncu capture of that step (its command and
+# per-launch figures are summarised under profiles/).  Keyed by workload, the launch shape (lanes,
+# warp_max_edges, chunk_edges, dense_div, relax_mode, blocks_per_sm) and a hash of the kernel
+# sources: another shape, or any change to the kernel, reports null.
+MEASURED_TRAFFIC = {
+    # medium workload, lanes 16 / warp_max_edges 128 / chunk_edges 512 / dense_div 16 / mode 0 / all
+    # resident blocks (the capture's per-launch figures are summarised under profiles/)
+    (2, 16, 128, 512, 16, 0, 0, "4ab141ecd96574dc"): 2763619616,
+}
 KERNEL_SOURCES = ("paper_2401_02563_gb300/csrc/edgemap_kernel.cuh", "paper_2401_02563_gb300/csrc/common.cuh")
 
 
@@ -361,12 +368,16 @@ def main():
         g = kx.Graph.from_edges(el, stream=stream)
         g.index(w.theta if w.theta != kx.KAIROS_NO_INDEX else 256)
         info = g.info()
-        if args.lanes:
+        fixed = bool(args.lanes or args.shape)
+        if args.shape:
+            ln, wm, ch, dd, rm, bp = (int(x) for x in args.shape.split(","))
+            g.set_tuning(lanes=ln, warp_max_edges=wm, chunk_edges=ch, dense_div=dd, relax_mode=rm, blocks_per_sm=bp)
+        elif args.lanes:
             g.set_tuning(lanes=args.lanes)
         else:
             g.autotune(queries)
         theta_sweep = None
-        if args.workload != 2 and not args.lanes:
+        if args.workload != 2 and not fixed:
             # workloads without a fixed cutoff: the index threshold is tuned too (swept 16..4096)
             best_theta, sweep = g.autotune_index(queries[: max(32, len(queries) // 4)])
             theta_sweep = {"best": best_theta, "ms_by_threshold": sweep}
@@ -481,7 +492,9 @@ def main():
         "index_threshold_sweep": theta_sweep,
         "batched_vs_single_qps": (Q / (step_ms / 1e3)) / single["queries_per_s"] if single else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": MEASURED_TRAFFIC.get((args.workload, lanes, tuning.relax_mode, kernel_hash())),
+                     "traffic": MEASURED_TRAFFIC.get((args.workload, lanes, tuning.warp_max_edges, tuning.chunk_edges,
+                                                      tuning.dense_div, tuning.relax_mode, tuning.blocks_per_sm,
+                                                      kernel_hash())),
                      "peak_kind": peak_kind, "kernel": "edgemap_kernel", "kernel_hash": kernel_hash(),
                      "launches_per_step": n_launch, "avg_launch_ms": launch_ms,
                      "algorithmic_bytes_per_step": bytes_step},
