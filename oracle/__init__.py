@@ -1,6 +1,7 @@
 """ORACLE -- test infrastructure only.
 
-Plain CPU statement of the temporal path queries (earliest arrival, latest departure),
+Plain CPU statement of the temporal path queries (earliest arrival, latest departure,
+fastest path),
 used by the test suite, the package smoke check and the CPU-baseline leg of the
 benchmark, and by nothing in the library.  `oracle.c` holds the single-threaded one-pass
 scans; this module loads it and adds pure-Python brute force over simple paths for tiny
@@ -14,7 +15,8 @@ with the source initialised to the window start):
   * consecutive edges e, f of a path: t_f >= t_e + lam_e (Succeeds) or > (StrictlySucceeds);
     the first edge may depart at ta and the last may arrive at tw under either predicate;
   * EA[s] = ta; EA[v] = min arrival over paths s -> v; LD[x] = tw; LD[u] = max first
-    departure over paths u -> x; unreachable = 0xFFFFFFFF.
+    departure over paths u -> x; FP[s] = 0; FP[v] = min (arrival - first departure) over
+    paths s -> v; unreachable = 0xFFFFFFFF.
 """
 from __future__ import annotations
 
@@ -53,7 +55,7 @@ def _load():
         L = ctypes.CDLL(_LIB)
         L.oracle_time_order.argtypes = [ctypes.c_int64, _P, _P]
         L.oracle_time_order.restype = ctypes.c_int
-        for fn in ("oracle_earliest_arrival", "oracle_latest_departure"):
+        for fn in ("oracle_earliest_arrival", "oracle_latest_departure", "oracle_fastest"):
             f = getattr(L, fn)
             f.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int32,
                           ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _P]
@@ -111,6 +113,15 @@ class Oracle:
                                              int(strict), out.ctypes.data)
         if rc != 0:
             raise ValueError("oracle_latest_departure: invalid arguments")
+        return out
+
+    def fastest(self, s: int, ta: int, tw: int, strict: int = 0) -> np.ndarray:
+        """Fastest-path durations from s (min arrival - first departure; fp[s] = 0)."""
+        out = np.empty(self.n, np.uint32)
+        rc = _load().oracle_fastest(self.n, self.m, *self._ptrs(), int(s), int(ta), int(tw), int(strict),
+                                    out.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle_fastest: invalid arguments or allocation failure")
         return out
 
     def query(self, q) -> np.ndarray:
@@ -222,4 +233,36 @@ def brute_latest_departure(n, src, dst, t, lam, x, ta, tw, strict=0, used=None):
             onpath.discard(u)
 
     go(x, tw, True, {x})
+    return np.array(out, np.uint32)
+
+
+def brute_fastest(n, src, dst, t, lam, s, ta, tw, strict=0):
+    """Enumerate every vertex-simple time-respecting path from s and keep, per end vertex,
+    the minimum of (arrival - first departure).  Cutting a cycle out of a time-respecting
+    walk keeps its end and moves its first departure no earlier, so simple paths suffice."""
+    out = [UNREACHED] * n
+    out[s] = 0
+    adj = [[] for _ in range(n)]
+    for e in range(len(src)):
+        adj[int(src[e])].append(e)
+
+    def go(u, arrival, start, onpath):
+        for e in adj[u]:
+            te, le = int(t[e]), int(lam[e])
+            if not _usable(te, le, ta, tw):
+                continue
+            first = start is None
+            if not first and (te <= arrival if strict else te < arrival):
+                continue
+            v = int(dst[e])
+            if v in onpath:
+                continue
+            st = te if first else start
+            if te + le - st < out[v]:
+                out[v] = te + le - st
+            onpath.add(v)
+            go(v, te + le, st, onpath)
+            onpath.discard(v)
+
+    go(s, ta, None, {s})
     return np.array(out, np.uint32)

@@ -25,6 +25,10 @@
  * maximum first departure time over time-respecting paths from u to x in the window;
  * UNREACHED otherwise.
  *
+ * Fastest path from s (also a "minimal temporal path" of Sec. 2.3, defined by the same
+ * reference): fp[s] = 0, and for v != s the minimum of (arrival - first departure) over
+ * time-respecting paths from s to v in the window; UNREACHED otherwise.
+ *
  * Algorithm: the one-pass scan over the time-ordered edge stream of that reference
  * (credited in Sec. 7): edges are visited in ascending t (descending for latest
  * departure), and every edge sharing the same t is re-swept until nothing changes, which
@@ -222,4 +226,119 @@ int oracle_certify_ea(int64_t n, int64_t m, const int32_t *src, const int32_t *d
         }
     free(seen);
     return 0;
+}
+
+/*
+ * Fastest paths from s within [ta, tw]; out[n] (durations).  The reference's one-pass
+ * fastest-path scan: every vertex v keeps the (start, arrival) pairs of the paths found so
+ * far that no other pair dominates (a pair dominates another when it starts no earlier and
+ * arrives no later), sorted by start.  Edges are visited in ascending t (equal t re-swept
+ * until nothing changes).  An edge (u, v, t, lam) out of s starts a path (t, t + lam); out of
+ * another u it extends the pair of u with the latest start among those arriving in time
+ * (arrival <= t, < under StrictlySucceeds), which is the pair with the largest such
+ * arrival; the result (start, t + lam) joins v's pairs and fp[v] = min(fp[v], t + lam -
+ * start).  Pairs are plain arrays grown with realloc and kept sorted by insertion.
+ */
+typedef struct {
+    uint32_t *s, *a; /* starts ascending, arrivals ascending */
+    int64_t len, cap;
+} pair_list;
+
+/* Insert (s, a) unless a pair dominates it; drop the pairs it dominates.  Returns 1 when
+ * the list changed, 0 when not, -1 on allocation failure. */
+static int pairs_insert(pair_list *L, uint32_t s, uint32_t a) {
+    for (int64_t i = 0; i < L->len; ++i)
+        if (L->s[i] >= s && L->a[i] <= a) return 0; /* dominated */
+    int64_t w = 0;
+    for (int64_t i = 0; i < L->len; ++i)
+        if (!(L->s[i] <= s && L->a[i] >= a)) { /* keep what the new pair does not dominate */
+            L->s[w] = L->s[i];
+            L->a[w] = L->a[i];
+            ++w;
+        }
+    L->len = w;
+    if (L->len == L->cap) {
+        int64_t nc = L->cap ? 2 * L->cap : 4;
+        uint32_t *ns = (uint32_t *)realloc(L->s, (size_t)nc * sizeof(uint32_t));
+        if (!ns) return -1;
+        L->s = ns;
+        uint32_t *na = (uint32_t *)realloc(L->a, (size_t)nc * sizeof(uint32_t));
+        if (!na) return -1;
+        L->a = na;
+        L->cap = nc;
+    }
+    int64_t p = L->len; /* sorted position by start */
+    while (p > 0 && L->s[p - 1] > s) {
+        L->s[p] = L->s[p - 1];
+        L->a[p] = L->a[p - 1];
+        --p;
+    }
+    L->s[p] = s;
+    L->a[p] = a;
+    ++L->len;
+    return 1;
+}
+
+int oracle_fastest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                   const uint32_t *lam, const uint32_t *perm, int32_t s, uint32_t ta, uint32_t tw, int strict,
+                   uint32_t *out) {
+    if (check_common(n, m, src, dst, t, lam, perm, s, ta, tw, out)) return -1;
+    pair_list *P = (pair_list *)calloc((size_t)n, sizeof(pair_list));
+    uint64_t *best = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    int rc = 0;
+    if (!P || !best) {
+        rc = -1;
+        goto done;
+    }
+    for (int64_t v = 0; v < n; ++v) best[v] = UINT64_MAX;
+    best[s] = 0;
+    int64_t k = 0;
+    while (k < m && t[perm[k]] < ta) ++k; /* edges departing before the window */
+    while (k < m && t[perm[k]] <= tw) {
+        uint32_t now = t[perm[k]];
+        int64_t end = k;
+        while (end < m && t[perm[end]] == now) ++end;
+        int again = 1;
+        while (again) {
+            again = 0;
+            for (int64_t j = k; j < end; ++j) {
+                uint32_t e = perm[j];
+                uint64_t arrive = (uint64_t)now + lam[e];
+                if (arrive > tw) continue; /* leaves the window */
+                int32_t u = src[e], v = dst[e];
+                if (v == s) continue; /* a path back to s never beats fp[s] = 0 or a fresh start */
+                uint32_t start;
+                if (u == s) {
+                    start = now; /* depart s now: no later start exists for this edge */
+                } else {
+                    const pair_list *L = &P[u];
+                    int64_t i = L->len - 1; /* largest arrival that is in time */
+                    while (i >= 0 && (strict ? !(L->a[i] < now) : !(L->a[i] <= now))) --i;
+                    if (i < 0) continue; /* u not reached in time */
+                    start = L->s[i];
+                }
+                int ch = pairs_insert(&P[v], start, (uint32_t)arrive);
+                if (ch < 0) {
+                    rc = -1;
+                    goto done;
+                }
+                if (ch) {
+                    if (arrive - start < best[v]) best[v] = arrive - start;
+                    again = 1; /* a new pair may enable another edge of this instant */
+                }
+            }
+        }
+        k = end;
+    }
+    for (int64_t v = 0; v < n; ++v) out[v] = best[v] == UINT64_MAX ? UNREACHED : (uint32_t)best[v];
+done:
+    if (P) {
+        for (int64_t v = 0; v < n; ++v) {
+            free(P[v].s);
+            free(P[v].a);
+        }
+        free(P);
+    }
+    free(best);
+    return rc;
 }

@@ -1,6 +1,7 @@
 """Pins for the oracle, checked against things other than itself: a hand-worked example,
 brute force over simple paths, textbook reductions, the mirror identity between the two
-query kinds, and invariants that the definitions fix.  CPU only."""
+query kinds, the identity between fastest paths and earliest arrival over start times, and
+invariants that the definitions fix.  CPU only."""
 import json
 import os
 from collections import deque
@@ -10,8 +11,8 @@ import pytest
 
 import oracle
 import synth
-from oracle import (C_MIRROR, UNREACHED, Oracle, brute_earliest_arrival, brute_latest_departure,
-                    certify_ea, mirror_edges)
+from oracle import (C_MIRROR, UNREACHED, Oracle, brute_earliest_arrival, brute_fastest,
+                    brute_latest_departure, certify_ea, mirror_edges)
 from synth import EA, LD, Query
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -44,6 +45,11 @@ def test_hand_worked_example():
         assert brute.tolist() == c["expect"], c
         if "admissible" in c:
             assert orc.admissible(q, got) == c["admissible"]
+    for c in g["fastest_cases"]:
+        got = orc.fastest(c["vertex"], c["ta"], c["tw"], c["strict"])
+        assert got.tolist() == c["expect"], c
+        brute = brute_fastest(el.n, el.src, el.dst, el.t, el.lam, c["vertex"], c["ta"], c["tw"], c["strict"])
+        assert brute.tolist() == c["expect"], c
 
 
 def _tiny_cases(count):
@@ -217,3 +223,81 @@ def test_empty_graph_and_isolated_source():
     orc = Oracle(el)
     assert orc.earliest_arrival(2, 3, 9).tolist() == [UNREACHED, UNREACHED, 3, UNREACHED]
     assert orc.latest_departure(1, 3, 9).tolist() == [UNREACHED, 9, UNREACHED, UNREACHED]
+
+
+# ---- fastest paths --------------------------------------------------------------------
+
+def start_times(el, s, ta, tw):
+    """Distinct departure times of s's usable out-edges (t >= ta, t + lam <= tw)."""
+    m = (el.src == s) & (el.t >= ta) & (el.t.astype(np.uint64) + el.lam <= tw)
+    return sorted(set(int(x) for x in el.t[m]))
+
+
+def fastest_by_start_times(orc, el, s, ta, tw, strict):
+    """min over start times d of EA_[d, tw](v) - d: every path starting at d is a candidate
+    of EA from d, and EA from d is the end of a path starting at or after d."""
+    best = np.full(el.n, UNREACHED, np.uint64)
+    for d in start_times(el, s, ta, tw):
+        ea = orc.earliest_arrival(s, d, tw, strict).astype(np.uint64)
+        ok = ea != UNREACHED
+        best[ok] = np.minimum(best[ok], ea[ok] - d)
+    best[s] = 0
+    return best.astype(np.uint32)
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_fastest_brute_force_tiny_graphs(strict):
+    """The one-pass pair scan against enumeration of simple paths, on the tiny multigraphs
+    (self-loops, parallel edges, zero durations)."""
+    for el, v, ta, tw in _tiny_cases(1500):
+        got = Oracle(el).fastest(v, ta, tw, strict)
+        want = brute_fastest(el.n, el.src, el.dst, el.t, el.lam, v, ta, tw, strict)
+        assert np.array_equal(got, want), (el.src, el.dst, el.t, el.lam, v, ta, tw)
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_fastest_equals_min_over_start_times(tiny_workload, strict):
+    """On the 10^5-edge workload graph: the pair scan equals the minimum, over the source's
+    departure times d, of earliest arrival from d minus d (the pinned earliest-arrival scan)."""
+    el, orc = tiny_workload
+    for k in range(4):
+        s = int(np.flatnonzero(np.bincount(el.src, minlength=el.n))[7 * k + 3])
+        ta, tw = (0, 2**20 - 1) if k % 2 == 0 else (1 << 18, 3 << 18)
+        got = orc.fastest(s, ta, tw, strict)
+        assert np.array_equal(got, fastest_by_start_times(orc, el, s, ta, tw, strict)), (s, ta, tw)
+
+
+def test_fastest_reductions():
+    """(1) Every edge at t = 0 with zero duration: duration 0 on exactly the BFS-reachable set.
+    (2) A chain s -> 1 -> ... -> k with edge i at time i and duration 1 (plus slower early
+    copies): the fastest duration to vertex j is j (one path, no waiting).  (3) Waiting
+    counts: a later direct edge beats an earlier two-hop path with a long layover."""
+    for seed in range(10):
+        el = synth.random_small(40, 90, 0x7500 + seed, t_max=0, lam_max=0)
+        s = seed % 40
+        got = Oracle(el).fastest(s, 0, 5)
+        dist = _bfs(el.n, el.src, el.dst, s)
+        assert [g == 0 for g in got] == [d >= 0 for d in dist]
+        assert all(g in (0, UNREACHED) for g in got)
+    k = 8
+    rows = [(i, i + 1, i, 1) for i in range(k)] + [(i, i + 1, 0, 3) for i in range(1, k)]
+    got = Oracle(from_rows(k + 1, rows)).fastest(0, 0, 100)
+    assert got.tolist() == list(range(k + 1))
+    rows = [(0, 1, 0, 1), (1, 2, 50, 1), (0, 2, 60, 5)]
+    got = Oracle(from_rows(3, rows)).fastest(0, 0, 100)
+    assert got.tolist() == [0, 1, 5]  # 0->1->2 takes 0..51; the direct edge takes 5
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_fastest_invariants(tiny_workload, strict):
+    """fp[v] <= ea[v] - ta (the earliest-arrival path starts at or after ta); fp is finite
+    exactly where ea is; every finite fp is at most tw - ta."""
+    el, orc = tiny_workload
+    for s in (3, 99, 1234):
+        ta, tw = 1 << 17, (1 << 20) - 1
+        fp = orc.fastest(s, ta, tw, strict).astype(np.int64)
+        ea = orc.earliest_arrival(s, ta, tw, strict).astype(np.int64)
+        reached = ea != UNREACHED
+        assert np.array_equal(fp != UNREACHED, reached)
+        assert np.all(fp[reached] <= ea[reached] - ta)
+        assert np.all(fp[reached] <= tw - ta)
