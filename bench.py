@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-fastest", action="store_true")
+    p.add_argument("--fastest-queries", type=int, default=16)
     p.add_argument("--serve-rates", default="1000,4000,16000")
     p.add_argument("--serve-queries", type=int, default=400)
     p.add_argument("--serve-slots", type=int, default=16)
@@ -255,6 +257,30 @@ def measure_serving(torch, kx, g, el, span, rates, per_rate, slots, slice_rounds
     return res
 
 
+def measure_fastest(torch, kx, g, el, ta, tw, count):
+    """Fastest-path queries (kairos_fastest_path) from `count` seeded sources with an out-edge,
+    window [ta, tw], device output.  Lane work (relaxed edges over all start-time lanes)
+    comes from one untimed pass with statistics; the timed pass runs without them."""
+    srcs = synth.pick_vertices(el, count, 0xFA57, True, False)
+    out = torch.empty(el.n, dtype=torch.int32, device="cuda")
+    starts = relaxed = launches = 0
+    for s in srcs:
+        st = g.fastest_path(s, ta, tw, out, 0, True)
+        starts += st.start_times
+        relaxed += st.relaxed_edges
+        launches += st.launches
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in srcs:
+        g.fastest_path(s, ta, tw, out)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"queries": count, "queries_per_s": count / dt, "ms_per_query": dt * 1e3 / count,
+            "start_times_per_query": starts / count, "launches_per_query": launches / count,
+            "lane_gteps": relaxed / dt / 1e9, "window": [int(ta), int(tw)], "sources": "0xFA57 draw",
+            "lanes": g.tuning().lanes, "sources_list": srcs[:4]}
+
+
 def replica_reduce(step_ms, te_step, world, device):
     """Across replicas: the slowest rank's step time and the total traversed edges.  Replicas
     hold the whole graph and answer their own query shard, so this is the only exchange."""
@@ -269,8 +295,10 @@ def replica_reduce(step_ms, te_step, world, device):
     return float(t.item()), int(e.item())
 
 
-def cpu_baseline(el, queries, budget_s=20.0):
-    """The oracle as it stands, single-threaded on a host core, on a bounded sample."""
+def cpu_baseline(el, queries, budget_s=20.0, fastest=None):
+    """The oracle as it stands, single-threaded on a host core, on a bounded sample.  With
+    `fastest` (the GPU fastest-path measurement), also the oracle's fastest-path pair scan
+    on its first sources (up to about 10 s)."""
     import oracle
     t0 = time.perf_counter()
     orc = oracle.Oracle(el)
@@ -294,7 +322,21 @@ def cpu_baseline(el, queries, budget_s=20.0):
                 break
         if scan_s > min(budget_s, 1.0):
             break
-    return {"value": te / scan_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    fast = None
+    if fastest:
+        ta, tw = fastest["window"]
+        srcs = synth.pick_vertices(el, fastest["queries"], 0xFA57, True, False)
+        f_s, f_n = 0.0, 0
+        for s in srcs:
+            t1 = time.perf_counter()
+            orc.fastest(s, ta, tw, 0)
+            f_s += time.perf_counter() - t1
+            f_n += 1
+            if f_s > budget_s / 2:
+                break
+        fast = {"queries_per_s": f_n / f_s, "sample": f"{f_n} of the {fastest['queries']} fastest-path sources, "
+                                                      f"one-pass pair scan on 1 host core"}
+    return {"fastest": fast, "value": te / scan_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{len(done)} runs over {len(queries)} queries ({sum(queries[i].kind == 0 for i in done)} EA, "
                       f"{sum(queries[i].kind == 1 for i in done)} LD), one-pass scans on 1 host core; "
                       f"time-order sort ({sort_s:.1f} s) excluded as preprocessing",
@@ -469,13 +511,16 @@ def main():
             rates = [float(x) for x in args.serve_rates.split(",") if x]
             served = measure_serving(torch, kx, g, el, w.graph.t_span, rates, args.serve_queries, args.serve_slots,
                                      args.serve_slice)
+        fastest = None
+        if not args.no_fastest:
+            fastest = measure_fastest(torch, kx, g, el, queries[0].ta, queries[0].tw, args.fastest_queries)
         g.close()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    cpu = None if args.no_cpu else cpu_baseline(el, queries)
+    cpu = None if args.no_cpu else cpu_baseline(el, queries, fastest=fastest)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -499,6 +544,7 @@ def main():
                      "launches_per_step": n_launch, "avg_launch_ms": launch_ms,
                      "algorithmic_bytes_per_step": bytes_step},
         "served": served,
+        "fastest": fastest,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * n_launch,

@@ -174,6 +174,27 @@ kairos_status kairos_latest_departure(kairos_graph *g, int32_t dst, uint32_t ta,
 kairos_status kairos_batch_query(kairos_graph *g, const kairos_query *queries, int32_t n, uint32_t *out,
                                  kairos_query_stats *stats);
 
+/* Fastest paths from src within [ta, tw] (Sec. 2.3 names fastest paths among the minimal
+ * temporal paths; the definition is that of the paper's reference on temporal path
+ * problems): out[v] = the minimum over time-respecting paths P from src to v inside the
+ * window of (arrival(P) - first departure(P)); out[src] = 0; KAIROS_UNREACHED otherwise.
+ * strict: 0 Succeeds, 1 StrictlySucceeds between consecutive edges.
+ * Method: one earliest-arrival lane per distinct departure time d of src's usable
+ * out-edges (window [d, tw]), packed tuning.lanes per launch on the batched edge-map, then
+ * out[v] = min over d of (EA_d[v] - d) on the device.  out: uint32_t[n], host or device,
+ * owned by the caller.  stats (may be NULL): start times, edge-map launches and relaxed
+ * edges summed over the lanes (asking for it counts relaxations, which costs some time).
+ * Synchronous.  Errors: INVALID_ARG (NULL graph or out, src out of range, ta > tw,
+ * tw > KAIROS_TIME_MAX, strict not 0/1), TIMEOUT, OOM, CUDA. */
+typedef struct {
+    uint64_t start_times;    /* distinct departure times of src's usable out-edges */
+    uint64_t launches;       /* edge-map launches */
+    uint64_t relaxed_edges;  /* sum over the start-time lanes of their relaxed edges */
+} kairos_fastest_stats;
+
+kairos_status kairos_fastest_path(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, int32_t strict,
+                                  uint32_t *out, kairos_fastest_stats *stats);
+
 /* ---- launch shape ----------------------------------------------------------------- */
 
 kairos_status kairos_get_tuning(const kairos_graph *g, kairos_tuning *t);

@@ -88,6 +88,10 @@ class kairos_result_info(ctypes.Structure):
                 ("checksum", ctypes.c_uint64), ("latency_ms", ctypes.c_double)]
 
 
+class kairos_fastest_stats(ctypes.Structure):
+    _fields_ = [("start_times", ctypes.c_uint64), ("launches", ctypes.c_uint64), ("relaxed_edges", ctypes.c_uint64)]
+
+
 # Every function the header declares, with its ctypes signature.
 SIGNATURES = {
     "kairos_graph_build": (ctypes.c_int, [ctypes.POINTER(kairos_edge_list), ctypes.POINTER(kairos_graph_opts),
@@ -99,6 +103,8 @@ SIGNATURES = {
     "kairos_latest_departure": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, _P]),
     "kairos_batch_query": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32, _P,
                                           ctypes.POINTER(kairos_query_stats)]),
+    "kairos_fastest_path": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32, _P,
+                                           ctypes.POINTER(kairos_fastest_stats)]),
     "kairos_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
     "kairos_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
     "kairos_autotune": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32,
@@ -269,6 +275,16 @@ def kairos_latest_departure(g, n, dst, ta, tw, out):
     return out
 
 
+def kairos_fastest_path(g, n, src, ta, tw, out, strict=0, want_stats=False):
+    """Fastest-path durations from src into out (uint32[n], host or device); returns the
+    kairos_fastest_stats when want_stats (relaxations are then counted)."""
+    _check_out(out, n)
+    st = kairos_fastest_stats() if want_stats else None
+    _check(lib().kairos_fastest_path(g, int(src), int(ta), int(tw), int(strict), _ptr(out),
+                                     ctypes.byref(st) if want_stats else None), "kairos_fastest_path")
+    return st
+
+
 def kairos_earliest_arrival_noalloc(g, n, src, ta, tw, out):
     """Earliest arrival that allocates no device memory; out must be a CUDA tensor."""
     _check_out(out, n)
@@ -413,6 +429,9 @@ class Graph:
 
     def latest_departure(self, dst, ta, tw, out):
         return kairos_latest_departure(self.handle, self.n, dst, ta, tw, out)
+
+    def fastest_path(self, src, ta, tw, out, strict=0, want_stats=False):
+        return kairos_fastest_path(self.handle, self.n, src, ta, tw, out, strict, want_stats)
 
     def batch(self, queries, out, want_stats=True):
         return kairos_batch_query(self.handle, self.n, queries, out, want_stats)

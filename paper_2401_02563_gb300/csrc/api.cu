@@ -249,7 +249,7 @@ void drop_graph(kairos_graph *g) {
 // enqueued back to back (one counter slot each) and read back once; when the outputs are
 // device memory and the graph has its own stream, the whole sequence is captured into a
 // CUDA graph, which is replayed while the same call repeats.
-kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_t nq, uint32_t *out,
+kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_t nq, uint32_t *out,
                                  kairos_query_stats *stats, int lanes) {
     const int64_t n = g->n;
     const bool dev = out ? device_ptr(out) : true;
@@ -492,6 +492,7 @@ void kairos_graph_free(kairos_graph *g) {
         cudaStreamSynchronize(g->stream);
         cudaGetLastError();
         release_work_arrays(g);
+        release_fastest_scratch(g);
         free_csr(g->A, &g->fwd);
         free_csr(g->A, &g->rev);
         if (g->work.ctr_host) cudaFreeHost(g->work.ctr_host);

@@ -177,6 +177,13 @@ cudaError_t edgemap_launch_w(const EdgeMapArgs &a, int lam_bits, int grid, cudaS
 template <int W>
 int edgemap_max_blocks_w(int lam_bits, int relax_mode);
 
+// Run queries through the batched edge-map, `lanes` per launch (api.cu; shared by the query
+// calls, the autotuner and fastest paths).  out == nullptr discards the labels.
+kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_t nq, uint32_t *out,
+                                 kairos_query_stats *stats, int lanes);
+// Free the fastest-path scratch of a graph (fastest.cu).
+void release_fastest_scratch(kairos_graph *g);
+
 // ---- device build ------------------------------------------------------------------------
 
 // Time-sorted CSR of (key_src -> key_dst) edges.  mirror != 0 builds the reversed,
@@ -228,6 +235,10 @@ struct kairos_graph {
         size_t ctr_slots = 0;
         cudaGraphExec_t graph_exec = nullptr;     // the last captured call
         std::string graph_key;
+        // fastest paths: label rows of one pass of start-time lanes, the running minimum
+        // (host outputs) and the start times of the pass
+        uint32_t *fast_rows = nullptr, *fast_best = nullptr, *fast_d = nullptr;
+        int64_t fast_rows_cap = 0;
     } work;
     int last_launches = 0;
     int64_t graph_launches = 0;
