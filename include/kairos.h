@@ -121,6 +121,11 @@ typedef struct {
                                (suits few active lanes); 1: lower it with a fire-and-forget
                                atomic for every usable edge and take the next frontier from the
                                bitmap of touched heads */
+    int32_t concurrent;     /* launches of one call kept in flight together, each on its own stream
+                               and workspace with 1/concurrent of the resident blocks (unless
+                               blocks_per_sm is set): 1 or 2 (0 means 1).  2 lets one launch's
+                               sparse final rounds overlap another's busy ones; it applies when the
+                               outputs are device memory and the call has two or more launches */
 } kairos_tuning;
 
 typedef struct {

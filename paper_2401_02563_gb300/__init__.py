@@ -68,7 +68,8 @@ class kairos_query_stats(ctypes.Structure):
 
 class kairos_tuning(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("warp_max_edges", ctypes.c_int32),
-                ("chunk_edges", ctypes.c_int32), ("dense_div", ctypes.c_int32), ("relax_mode", ctypes.c_int32)]
+                ("chunk_edges", ctypes.c_int32), ("dense_div", ctypes.c_int32), ("relax_mode", ctypes.c_int32),
+                ("concurrent", ctypes.c_int32)]
 
 
 class kairos_graph_info(ctypes.Structure):

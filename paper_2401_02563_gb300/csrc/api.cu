@@ -76,15 +76,25 @@ void release_work_arrays(kairos_graph *g) {
     w.arr = w.prev = w.bm = w.bigb = w.chunk_owner = w.stage = nullptr;
     w.queue = nullptr;
     w.big = nullptr;
+    A.put(w.arr2);
+    A.put(w.prev2);
+    A.put(w.bm2);
+    A.put(w.queue2);
+    A.put(w.big2);
+    A.put(w.bigb2);
+    A.put(w.chunk_owner2);
+    w.arr2 = w.prev2 = w.bm2 = w.bigb2 = w.chunk_owner2 = nullptr;
+    w.queue2 = nullptr;
+    w.big2 = nullptr;
     w.lanes = 0;
     w.cap_big = w.cap_chunks = 0;
     w.bytes = 0;
 }
 
-kairos_status ensure_work(kairos_graph *g, int lanes, bool need_stage) {
+kairos_status ensure_work(kairos_graph *g, int lanes, bool need_stage, bool need_second) {
     auto &w = g->work;
     const int wm = g->tuning.warp_max_edges, ch = g->tuning.chunk_edges;
-    if (w.arr && w.lanes == lanes && w.warp_max == wm && w.chunk == ch) {
+    if (w.arr && w.lanes == lanes && w.warp_max == wm && w.chunk == ch && (!need_second || w.arr2)) {
         if (need_stage && !w.stage) {
             w.stage = (uint32_t *)g->A.get((size_t)g->n * lanes * 4);
             if (!w.stage) return fail(KAIROS_ERR_OOM, "query workspace: device allocation failed");
@@ -114,18 +124,31 @@ kairos_status ensure_work(kairos_graph *g, int lanes, bool need_stage) {
     w.bigb = (uint32_t *)A.get((size_t)cap_big * lanes * 2 * 4);
     w.chunk_owner = (uint32_t *)A.get((size_t)cap_chunks * 4);
     if (need_stage) w.stage = (uint32_t *)A.get((size_t)n * lanes * 4);
-    if (!w.arr || !w.prev || !w.bm || !w.queue || !w.big || !w.bigb || !w.chunk_owner || (need_stage && !w.stage)) {
+    if (need_second) {
+        w.arr2 = (uint32_t *)A.get((size_t)n * lanes * 4);
+        w.prev2 = (uint32_t *)A.get((size_t)n * lanes * 4);
+        w.bm2 = (uint32_t *)A.get((size_t)nwords * 2 * 4);
+        w.queue2 = (int32_t *)A.get((size_t)n * 2 * 4);
+        w.big2 = (BigEntry *)A.get((size_t)cap_big * sizeof(BigEntry));
+        w.bigb2 = (uint32_t *)A.get((size_t)cap_big * lanes * 2 * 4);
+        w.chunk_owner2 = (uint32_t *)A.get((size_t)cap_chunks * 4);
+    }
+    if (!w.arr || !w.prev || !w.bm || !w.queue || !w.big || !w.bigb || !w.chunk_owner || (need_stage && !w.stage) ||
+        (need_second && (!w.arr2 || !w.prev2 || !w.bm2 || !w.queue2 || !w.big2 || !w.bigb2 || !w.chunk_owner2))) {
         release_work_arrays(g);
         return fail(KAIROS_ERR_OOM, "query workspace: device allocation failed");
     }
     KAIROS_CUDA(cudaMemsetAsync(w.chunk_owner, 0xFF, (size_t)cap_chunks * 4, g->stream), "workspace init");
+    if (need_second)
+        KAIROS_CUDA(cudaMemsetAsync(w.chunk_owner2, 0xFF, (size_t)cap_chunks * 4, g->stream), "workspace init");
     w.lanes = lanes;
     w.warp_max = wm;
     w.chunk = ch;
     w.cap_big = (uint32_t)cap_big;
     w.cap_chunks = (uint32_t)cap_chunks;
-    w.bytes = (size_t)n * lanes * 8 + (size_t)nwords * 8 + (size_t)n * 8 + cap_big * (sizeof(BigEntry) + lanes * 8) +
-              cap_chunks * 4 + (need_stage ? (size_t)n * lanes * 4 : 0);
+    const size_t set_bytes = (size_t)n * lanes * 8 + (size_t)nwords * 8 + (size_t)n * 8 +
+                             cap_big * (sizeof(BigEntry) + lanes * 8) + cap_chunks * 4;
+    w.bytes = set_bytes * (need_second ? 2 : 1) + (need_stage ? (size_t)n * lanes * 4 : 0);
     return KAIROS_OK;
 }
 
@@ -156,8 +179,9 @@ void lane_set(LaneParams &lp, int q, const kairos_query &Q, int64_t row) {
 }
 
 EdgeMapArgs make_args(kairos_graph *g, const Csr &c, const LaneParams &lp, uint32_t *out, int64_t stride,
-                      uint32_t *arr_alias, int count_relaxed, EdgeMapCtr *ctr) {
+                      uint32_t *arr_alias, int count_relaxed, EdgeMapCtr *ctr, int slot = 0) {
     auto &w = g->work;
+    const bool s2 = slot == 1;  // the second workspace (concurrent launches)
     const int64_t n = g->n, nwords = (n + 31) / 32;
     EdgeMapArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -168,15 +192,15 @@ EdgeMapArgs make_args(kairos_graph *g, const Csr &c, const LaneParams &lp, uint3
     a.fidx = c.fidx;
     a.fence = c.fence;
     a.n = n;
-    a.arr = arr_alias ? arr_alias : w.arr;
-    a.prev = w.prev;
-    a.bm[0] = w.bm;
-    a.bm[1] = w.bm + nwords;
-    a.queue[0] = w.queue;
-    a.queue[1] = w.queue + n;
-    a.big = w.big;
-    a.bigb = w.bigb;
-    a.chunk_owner = w.chunk_owner;
+    a.arr = arr_alias ? arr_alias : (s2 ? w.arr2 : w.arr);
+    a.prev = s2 ? w.prev2 : w.prev;
+    a.bm[0] = s2 ? w.bm2 : w.bm;
+    a.bm[1] = a.bm[0] + nwords;
+    a.queue[0] = s2 ? w.queue2 : w.queue;
+    a.queue[1] = a.queue[0] + n;
+    a.big = s2 ? w.big2 : w.big;
+    a.bigb = s2 ? w.bigb2 : w.bigb;
+    a.chunk_owner = s2 ? w.chunk_owner2 : w.chunk_owner;
     a.cap_big = w.cap_big;
     a.cap_chunks = w.cap_chunks;
     a.ctr = ctr;
@@ -253,9 +277,23 @@ kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs
                                  kairos_query_stats *stats, int lanes) {
     const int64_t n = g->n;
     const bool dev = out ? device_ptr(out) : true;
-    kairos_status st = ensure_work(g, lanes, out && !dev && lanes > 1);
+    // launches kept in flight together: two (second workspace and stream) when asked for, the
+    // outputs are device memory and the call has at least two launches
+    int64_t n_launch = 0;
+    for (int kind = 0; kind < 2; ++kind) {
+        int64_t c = 0;
+        for (int i = 0; i < nq; ++i) c += qs[i].kind == kind;
+        n_launch += (c + lanes - 1) / lanes;
+    }
+    const int C = (dev && g->tuning.concurrent >= 2 && n_launch >= 2) ? 2 : 1;
+    kairos_status st = ensure_work(g, lanes, out && !dev && lanes > 1, C == 2);
     if (st != KAIROS_OK) return st;
     auto &w = g->work;
+    if (C == 2 && !w.side) {
+        KAIROS_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking), "concurrent launches: stream");
+        KAIROS_CUDA(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming), "concurrent launches: event");
+        KAIROS_CUDA(cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming), "concurrent launches: event");
+    }
     g->last_kernel_ms = 0;
     cudaStream_t s = g->stream;
 
@@ -275,8 +313,9 @@ kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs
             uint32_t *o = nullptr, *alias = nullptr;
             for (int j = 0; j < k; ++j) lane_set(lp, j, qs[idx[c + j]], j);
             const uint32_t *host_src = nullptr;
+            const int slot = (int)(plan.size() % C);
             if (lanes == 1) {
-                alias = (out && dev) ? out + (int64_t)idx[c] * n : w.arr;
+                alias = (out && dev) ? out + (int64_t)idx[c] * n : (slot ? w.arr2 : w.arr);
                 o = out ? alias : nullptr;
                 if (out && !dev) host_src = w.arr;
             } else if (out) {
@@ -289,7 +328,7 @@ kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs
                 }
             }
             Planned P;
-            P.a = make_args(g, csr, lp, o, n, alias, stats != nullptr, nullptr);
+            P.a = make_args(g, csr, lp, o, n, alias, stats != nullptr, nullptr, slot);
             P.qid.assign(idx.begin() + c, idx.begin() + c + k);
             P.host_src = host_src;
             plan.push_back(std::move(P));
@@ -303,11 +342,17 @@ kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs
     int grid = edgemap_max_grid(lanes, g->lam_bits, g->tuning.relax_mode, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "edge-map: no resident launch shape (occupancy query failed)");
     if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
+    else if (C == 2) grid = std::max(1, bps / 2) * g->sm_count;  // both launches resident at once
 
     auto enqueue = [&](bool direct) -> kairos_status {
+        if (C == 2) {  // fork: the side stream starts after everything before this call
+            KAIROS_CUDA(cudaEventRecord(w.fork, s), "concurrent launches: fork");
+            KAIROS_CUDA(cudaStreamWaitEvent(w.side, w.fork, 0), "concurrent launches: fork");
+        }
         for (size_t i = 0; i < plan.size(); ++i) {
-            KAIROS_CUDA(cudaMemsetAsync(plan[i].a.ctr, 0, sizeof(EdgeMapCtr), s), "edge-map counters");
-            KAIROS_CUDA(edgemap_launch(plan[i].a, lanes, g->lam_bits, grid, s), "edge-map launch");
+            cudaStream_t si = (C == 2 && (i % 2)) ? w.side : s;
+            KAIROS_CUDA(cudaMemsetAsync(plan[i].a.ctr, 0, sizeof(EdgeMapCtr), si), "edge-map counters");
+            KAIROS_CUDA(edgemap_launch(plan[i].a, lanes, g->lam_bits, grid, si), "edge-map launch");
             if (direct && plan[i].host_src) {
                 const std::vector<int> &q = plan[i].qid;
                 for (size_t j = 0; j < q.size(); ++j)
@@ -315,6 +360,10 @@ kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs
                                                 (size_t)n * 4, cudaMemcpyDeviceToHost, s),
                                 "copy labels to host");
             }
+        }
+        if (C == 2) {  // join: the call's stream waits for the side stream's launches
+            KAIROS_CUDA(cudaEventRecord(w.join, w.side), "concurrent launches: join");
+            KAIROS_CUDA(cudaStreamWaitEvent(s, w.join, 0), "concurrent launches: join");
         }
         return KAIROS_OK;
     };
@@ -409,6 +458,7 @@ kairos_status kairos_graph_build(const kairos_edge_list *el, const kairos_graph_
     g->tuning.warp_max_edges = 128;
     g->tuning.chunk_edges = 512;
     g->tuning.dense_div = 16;
+    g->tuning.concurrent = 1;
     auto bail = [&](kairos_status st) {
         kairos_graph_free(g);
         return st;
@@ -499,6 +549,9 @@ void kairos_graph_free(kairos_graph *g) {
         g->A.put(g->work.ctrs);
         if (g->work.ctrs_host) cudaFreeHost(g->work.ctrs_host);
         if (g->work.graph_exec) cudaGraphExecDestroy(g->work.graph_exec);
+        if (g->work.side) cudaStreamDestroy(g->work.side);
+        if (g->work.fork) cudaEventDestroy(g->work.fork);
+        if (g->work.join) cudaEventDestroy(g->work.join);
         if (g->work.ev0) cudaEventDestroy(g->work.ev0);
         if (g->work.ev1) cudaEventDestroy(g->work.ev1);
         cudaGetLastError();
@@ -573,6 +626,7 @@ kairos_status kairos_set_tuning(kairos_graph *g, const kairos_tuning *t) {
         return fail(KAIROS_ERR_INVALID_ARG, "tuning: chunk_edges a multiple of 32 in [32, 2^24]");
     if (t->dense_div < 0) return fail(KAIROS_ERR_INVALID_ARG, "tuning: dense_div >= 0");
     if (t->relax_mode < 0 || t->relax_mode > 2) return fail(KAIROS_ERR_INVALID_ARG, "tuning: relax_mode is 0, 1 or 2");
+    if (t->concurrent < 0 || t->concurrent > 2) return fail(KAIROS_ERR_INVALID_ARG, "tuning: concurrent is 0, 1 or 2");
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning = *t;
     return KAIROS_OK;
@@ -647,6 +701,16 @@ kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32
     for (int b = 1; b < bps; ++b) {
         kairos_tuning c = win;
         c.blocks_per_sm = b;
+        kairos_status st = try_shape(c);
+        if (st != KAIROS_OK) {
+            g->tuning = base;
+            return st;
+        }
+    }
+    if (win.concurrent < 2) {  // two launches in flight, half the resident blocks each
+        kairos_tuning c = win;
+        c.concurrent = 2;
+        c.blocks_per_sm = 0;
         kairos_status st = try_shape(c);
         if (st != KAIROS_OK) {
             g->tuning = base;

@@ -235,6 +235,12 @@ struct kairos_graph {
         size_t ctr_slots = 0;
         cudaGraphExec_t graph_exec = nullptr;     // the last captured call
         std::string graph_key;
+        // the second workspace and stream of concurrent launches (tuning.concurrent == 2)
+        uint32_t *arr2 = nullptr, *prev2 = nullptr, *bm2 = nullptr, *bigb2 = nullptr, *chunk_owner2 = nullptr;
+        int32_t *queue2 = nullptr;
+        kairos::BigEntry *big2 = nullptr;
+        cudaStream_t side = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
         // fastest paths: label rows of one pass of start-time lanes, the running minimum
         // (host outputs) and the start times of the pass
         uint32_t *fast_rows = nullptr, *fast_best = nullptr, *fast_d = nullptr;

@@ -361,3 +361,35 @@ def test_relax_modes(tiny, lanes, mode):
         assert np.array_equal(got2[i], orc2.query(q)), q
     g2.close()
     g.set_tuning(lanes=1, relax_mode=0, warp_max_edges=128, chunk_edges=512)
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 16])
+def test_concurrent_launches(tiny, lanes):
+    """Two launches in flight on two streams and workspaces (tuning.concurrent = 2): the same
+    labels and counts as the oracle, on the graph's own stream (captured and replayed) and
+    on the default stream, with device outputs; host outputs fall back to one stream."""
+    el, orc, _ = tiny
+    n = el.n
+    qs = tiny_queries(el, 2 * lanes + 3)  # ragged, both kinds, at least three launches
+    want = [orc.query(q) for q in qs]
+    counts = [orc.admissible(q, w) for q, w in zip(qs, want)]
+    stream = torch.cuda.Stream()
+    for own_stream in (True, False):
+        g = kx.Graph.from_edges(el, stream=stream if own_stream else None)
+        g.index(16)
+        g.set_tuning(lanes=lanes, concurrent=2, warp_max_edges=32, chunk_edges=64)
+        with torch.cuda.stream(stream if own_stream else torch.cuda.default_stream()):
+            for rep in range(3):
+                out = torch.full((len(qs), n), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+                stats = g.batch(qs, out, want_stats=(rep != 1))
+                got = labels(out)
+                for i in range(len(qs)):
+                    assert np.array_equal(got[i], want[i]), (own_stream, rep, qs[i])
+                if stats:
+                    assert [s.relaxed_edges for s in stats] == counts
+        host = np.full((len(qs), n), 0x5A5A5A5A, np.uint32)
+        stats = g.batch(qs, host)
+        assert all(np.array_equal(host[i], want[i]) for i in range(len(qs)))
+        assert [s.relaxed_edges for s in stats] == counts
+        torch.cuda.synchronize()
+        g.close()
