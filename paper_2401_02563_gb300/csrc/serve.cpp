@@ -62,6 +62,10 @@ struct Session {
     uint64_t relaxed_base[MAX_LANES] = {};
     uint32_t admitted_round[MAX_LANES] = {};
     LaneParams lp{};
+    cudaStream_t s = nullptr;  // the session's stream (the graph's for EA, the server's own for LD)
+    bool launched = false;     // a slice is in flight
+    uint32_t last_seeded = 0;  // lanes seeded by the slice in flight (diagnostics)
+    std::chrono::steady_clock::time_point t_launch;
 };
 
 }  // namespace
@@ -74,6 +78,7 @@ struct kairos_server {
     int slice = 2;
     FILE *log = nullptr;  // KAIROS_SERVE_LOG: one line per session step (diagnostics)
     Session sess[2];
+    cudaStream_t side = nullptr;  // the latest-departure session's stream
     std::thread th;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -100,9 +105,11 @@ void free_session(const Allocator &A, Session &S) {
     if (S.stats_host) cudaFreeHost(S.stats_host);
     const int kind = S.kind;
     const Csr *csr = S.csr;
+    cudaStream_t st = S.s;
     S = Session();
     S.kind = kind;
     S.csr = csr;
+    S.s = st;
 }
 
 kairos_status alloc_session(kairos_graph *g, Session &S, int W) {
@@ -211,10 +218,12 @@ void admit(kairos_server *V, Session &S, int q, uint64_t id) {
     }
 }
 
-// One launch of S plus retirement of its finished lanes.  Returns the tickets finished.
-kairos_status step_session(kairos_server *V, Session &S, std::vector<std::pair<uint64_t, kairos_result_info>> &done) {
+// Enqueue one slice of S on its stream (seeds, the resumed launch, the counter read-back);
+// `share` sessions launch together, each with 1/share of the resident blocks when the graph's
+// tuning keeps two launches in flight.
+kairos_status launch_session(kairos_server *V, Session &S, int share) {
     kairos_graph *g = V->g;
-    cudaStream_t s = g->stream;
+    cudaStream_t s = S.s;
     EdgeMapArgs a = session_args(g, S);
     const uint32_t seeds = S.pending_seed;
     if (S.fresh) {
@@ -236,13 +245,26 @@ kairos_status step_session(kairos_server *V, Session &S, std::vector<std::pair<u
     int grid = edgemap_max_grid(S.W, g->lam_bits, a.relax_mode, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "serve: no resident launch shape");
     if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
-    const auto t_launch = clk::now();
+    else if (share == 2) grid = std::max(1, bps / 2) * g->sm_count;  // both slices resident at once
+    S.t_launch = clk::now();
     KAIROS_CUDA(edgemap_launch(a, S.W, g->lam_bits, grid, s), "serve: edge-map launch");
     KAIROS_CUDA(cudaMemcpyAsync(S.ctr_host, S.ctr, sizeof(EdgeMapCtr), cudaMemcpyDeviceToHost, s), "serve: counters");
-    KAIROS_CUDA(cudaStreamSynchronize(s), "serve: edge-map");
-    const double launch_ms = std::chrono::duration<double, std::milli>(clk::now() - t_launch).count();
+    S.launched = true;
+    S.last_seeded = seeds;
     S.fresh = false;
     S.pending_seed = 0;
+    return KAIROS_OK;
+}
+
+// Wait for S's slice, then retire its finished lanes (labels out, lanes reset).  Appends the
+// tickets finished to `done`.
+kairos_status finish_session(kairos_server *V, Session &S, std::vector<std::pair<uint64_t, kairos_result_info>> &done) {
+    kairos_graph *g = V->g;
+    cudaStream_t s = S.s;
+    S.launched = false;
+    const uint32_t seeds = S.last_seeded;
+    KAIROS_CUDA(cudaStreamSynchronize(s), "serve: edge-map");
+    const double launch_ms = std::chrono::duration<double, std::milli>(clk::now() - S.t_launch).count();
     const EdgeMapCtr &c = *S.ctr_host;
     if (c.err) {
         S.fresh = true;  // the state is unusable: fail the lanes and start over
@@ -338,14 +360,24 @@ void worker(kairos_server *V) {
                 }
             }
         }
-        // one launch per session with work, alternating which goes first
+        // one slice per session with work, alternating which goes first; when the graph's tuning
+        // keeps two launches in flight, both sessions' slices run at once on their own streams
         done.clear();
         kairos_status st = KAIROS_OK;
         {
             std::lock_guard<std::mutex> glk(V->g->mu);
+            const bool together = V->g->tuning.concurrent >= 2 && V->sess[0].running && V->sess[1].running;
             for (int k = 0; k < 2 && st == KAIROS_OK; ++k) {
                 Session &S = V->sess[(turn + k) & 1];
-                if (S.running) st = step_session(V, S, done);
+                if (!S.running) continue;
+                st = launch_session(V, S, together ? 2 : 1);
+                if (st == KAIROS_OK && !together) st = finish_session(V, S, done);
+            }
+            for (int k = 0; k < 2; ++k) {  // the slices still in flight (also after a failure)
+                Session &S = V->sess[(turn + k) & 1];
+                if (!S.launched) continue;
+                const kairos_status st2 = finish_session(V, S, done);
+                if (st == KAIROS_OK) st = st2;
             }
         }
         turn ^= 1;
@@ -417,6 +449,13 @@ kairos_status kairos_serve_create(kairos_graph *g, const kairos_serve_opts *opts
     V->sess[0].csr = &g->fwd;
     V->sess[1].kind = KAIROS_LD;
     V->sess[1].csr = &g->rev;
+    if (cudaStreamCreateWithFlags(&V->side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete V;
+        return fail(KAIROS_ERR_CUDA, "serve create: stream creation failed");
+    }
+    V->sess[0].s = g->stream;
+    V->sess[1].s = V->side;
     {
         std::lock_guard<std::mutex> lk(g->mu);
         for (int k = 0; k < 2; ++k) {
@@ -434,6 +473,7 @@ kairos_status kairos_serve_create(kairos_graph *g, const kairos_serve_opts *opts
             if (st != KAIROS_OK) {
                 free_session(g->A, V->sess[0]);
                 free_session(g->A, V->sess[1]);
+                cudaStreamDestroy(V->side);
                 delete V;
                 return st == KAIROS_ERR_OOM ? fail(st, "serve create: not enough device memory for two lanes") : st;
             }
@@ -445,6 +485,7 @@ kairos_status kairos_serve_create(kairos_graph *g, const kairos_serve_opts *opts
     } catch (...) {
         free_session(g->A, V->sess[0]);
         free_session(g->A, V->sess[1]);
+        cudaStreamDestroy(V->side);
         delete V;
         return fail(KAIROS_ERR_OOM, "serve create: thread start failed");
     }
@@ -502,8 +543,10 @@ void kairos_serve_destroy(kairos_server *V) {
     {
         std::lock_guard<std::mutex> lk(V->g->mu);
         cudaStreamSynchronize(V->g->stream);
+        cudaStreamSynchronize(V->side);
         free_session(V->g->A, V->sess[0]);
         free_session(V->g->A, V->sess[1]);
+        cudaStreamDestroy(V->side);
     }
     if (V->log) fclose(V->log);
     delete V;

@@ -49,13 +49,15 @@ def wait(server, ticket):
     return info
 
 
-@pytest.mark.parametrize("slots,slice_rounds", [(2, 1), (4, 2), (32, 4)])
-def test_served_results_equal_oracle_and_alone(served, slots, slice_rounds):
+@pytest.mark.parametrize("slots,slice_rounds,concurrent", [(2, 1, 1), (4, 2, 1), (32, 4, 1), (4, 2, 2), (16, 1, 2)])
+def test_served_results_equal_oracle_and_alone(served, slots, slice_rounds, concurrent):
+    """concurrent = 2: the two sessions' slices run at once on their own streams."""
     el, orc, g = served
-    qs = mixed_queries(el, 45, 0xB000 + slots)
+    qs = mixed_queries(el, 45, 0xB000 + slots + 7 * concurrent)
     alone = np.zeros((len(qs), el.n), np.uint32)
-    g.set_tuning(lanes=1)
+    g.set_tuning(lanes=1, concurrent=1)
     g.batch(qs, alone, want_stats=False)
+    g.set_tuning(concurrent=concurrent)
     server = kx.kairos_serve_create(g.handle, max_slots=slots, rounds_per_slice=slice_rounds)
     try:
         outs, tickets = [], []
@@ -70,6 +72,7 @@ def test_served_results_equal_oracle_and_alone(served, slots, slice_rounds):
         infos = [wait(server, t) for t in tickets]
     finally:
         kx.kairos_serve_destroy(server)
+        g.set_tuning(concurrent=1)
     for i, q in enumerate(qs):
         got = outs[i].cpu().numpy().view(np.uint32) if hasattr(outs[i], "cpu") else outs[i]
         want = orc.query(q)
