@@ -39,8 +39,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", type=int, default=2)
     p.add_argument("--lanes", type=int, default=0, help="0: autotune")
-    p.add_argument("--shape", default="", help="lanes,warp_max_edges,chunk_edges,dense_div,relax_mode,blocks_per_sm "
-                                               "(fixes the whole launch shape; no autotuning)")
+    p.add_argument("--shape", default="", help="lanes,warp_max_edges,chunk_edges,dense_div,relax_mode,blocks_per_sm"
+                                               "[,concurrent] (fixes the whole launch shape; no autotuning)")
     p.add_argument("--no-single", action="store_true", help="skip the one-query-per-launch comparison")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -57,12 +57,12 @@ def parse():
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per edge-map launch, averaged
 # over the 8 launches of one timed step, from one ncu capture of that step (its command and
 # per-launch figures are summarised under profiles/).  Keyed by workload, the launch shape (lanes,
-# warp_max_edges, chunk_edges, dense_div, relax_mode, blocks_per_sm) and a hash of the kernel
-# sources: another shape, or any change to the kernel, reports null.
+# warp_max_edges, chunk_edges, dense_div, relax_mode, blocks_per_sm, concurrent) and a hash of the
+# kernel sources: another shape, or any change to the kernel, reports null.
 MEASURED_TRAFFIC = {
     # medium workload, lanes 16 / warp_max_edges 128 / chunk_edges 512 / dense_div 16 / mode 0 / all
     # resident blocks (the capture's per-launch figures are summarised under profiles/)
-    (2, 16, 128, 512, 16, 0, 0, "4ab141ecd96574dc"): 2763619616,
+    (2, 16, 128, 512, 16, 0, 0, 1, "4ab141ecd96574dc"): 2763619616,
 }
 KERNEL_SOURCES = ("paper_2401_02563_gb300/csrc/edgemap_kernel.cuh", "paper_2401_02563_gb300/csrc/common.cuh")
 
@@ -412,8 +412,10 @@ def main():
         info = g.info()
         fixed = bool(args.lanes or args.shape)
         if args.shape:
-            ln, wm, ch, dd, rm, bp = (int(x) for x in args.shape.split(","))
-            g.set_tuning(lanes=ln, warp_max_edges=wm, chunk_edges=ch, dense_div=dd, relax_mode=rm, blocks_per_sm=bp)
+            f = [int(x) for x in args.shape.split(",")]
+            ln, wm, ch, dd, rm, bp = f[:6]
+            g.set_tuning(lanes=ln, warp_max_edges=wm, chunk_edges=ch, dense_div=dd, relax_mode=rm, blocks_per_sm=bp,
+                         concurrent=f[6] if len(f) > 6 else 1)
         elif args.lanes:
             g.set_tuning(lanes=args.lanes)
         else:
@@ -528,7 +530,8 @@ def main():
         "config": {"workload": f"{w.name}: {w.description}", "vertices": n, "edges": m, "queries_per_step": Q,
                    "index_threshold": theta_now, "lanes": lanes, "warp_max_edges": tuning.warp_max_edges,
                    "chunk_edges": tuning.chunk_edges, "blocks_per_sm": tuning.blocks_per_sm,
-                   "relax_mode": tuning.relax_mode, "dense_div": tuning.dense_div, "parallelism": f"replicas x{world}",
+                   "relax_mode": tuning.relax_mode, "dense_div": tuning.dense_div,
+                   "concurrent": max(1, tuning.concurrent), "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (graph {2 * (m * R + 8 * n) / 1e9:.1f} GB)"},
         "queries_per_s": world * Q / (step_ms / 1e3),
         "relaxed_edges_per_step": te_step, "scanned_edges_per_step": scanned_step,
@@ -539,7 +542,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": MEASURED_TRAFFIC.get((args.workload, lanes, tuning.warp_max_edges, tuning.chunk_edges,
                                                       tuning.dense_div, tuning.relax_mode, tuning.blocks_per_sm,
-                                                      kernel_hash())),
+                                                      max(1, tuning.concurrent), kernel_hash())),
                      "peak_kind": peak_kind, "kernel": "edgemap_kernel", "kernel_hash": kernel_hash(),
                      "launches_per_step": n_launch, "avg_launch_ms": launch_ms,
                      "algorithmic_bytes_per_step": bytes_step},
