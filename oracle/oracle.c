@@ -29,6 +29,10 @@
  * reference): fp[s] = 0, and for v != s the minimum of (arrival - first departure) over
  * time-respecting paths from s to v in the window; UNREACHED otherwise.
  *
+ * Shortest duration from s (the reference's "shortest path": least total travel time):
+ * sd[s] = 0, and for v != s the minimum of the sum of the edge durations over
+ * time-respecting paths from s to v in the window (waiting is free); UNREACHED otherwise.
+ *
  * Algorithm: the one-pass scan over the time-ordered edge stream of that reference
  * (credited in Sec. 7): edges are visited in ascending t (descending for latest
  * departure), and every edge sharing the same t is re-swept until nothing changes, which
@@ -325,6 +329,117 @@ int oracle_fastest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                 if (ch) {
                     if (arrive - start < best[v]) best[v] = arrive - start;
                     again = 1; /* a new pair may enable another edge of this instant */
+                }
+            }
+        }
+        k = end;
+    }
+    for (int64_t v = 0; v < n; ++v) out[v] = best[v] == UINT64_MAX ? UNREACHED : (uint32_t)best[v];
+done:
+    if (P) {
+        for (int64_t v = 0; v < n; ++v) {
+            free(P[v].s);
+            free(P[v].a);
+        }
+        free(P);
+    }
+    free(best);
+    return rc;
+}
+
+/*
+ * Shortest durations from s within [ta, tw]; out[n].  The reference's one-pass
+ * shortest-path scan: every vertex v keeps the (total duration, arrival) pairs of the paths
+ * found so far that no other pair dominates (a pair dominates another when its total is no
+ * larger and it arrives no later), sorted by arrival (totals then strictly decrease).
+ * Edges are visited in ascending t (equal t re-swept until nothing changes).  An edge
+ * (u, v, t, lam) out of s starts a path (lam, t + lam); out of another u it extends the
+ * pair of u with the smallest total among those arriving in time (arrival <= t, < under
+ * StrictlySucceeds), which is the in-time pair with the latest arrival; the result
+ * (total + lam, t + lam) joins v's pairs and sd[v] = min(sd[v], total + lam).
+ */
+static int dpairs_insert(pair_list *L, uint32_t d, uint32_t a) {
+    /* here pair_list.s holds totals, .a arrivals; sorted by arrival ascending */
+    for (int64_t i = 0; i < L->len; ++i)
+        if (L->s[i] <= d && L->a[i] <= a) return 0; /* dominated */
+    int64_t w = 0;
+    for (int64_t i = 0; i < L->len; ++i)
+        if (!(L->s[i] >= d && L->a[i] >= a)) {
+            L->s[w] = L->s[i];
+            L->a[w] = L->a[i];
+            ++w;
+        }
+    L->len = w;
+    if (L->len == L->cap) {
+        int64_t nc = L->cap ? 2 * L->cap : 4;
+        uint32_t *ns = (uint32_t *)realloc(L->s, (size_t)nc * sizeof(uint32_t));
+        if (!ns) return -1;
+        L->s = ns;
+        uint32_t *na = (uint32_t *)realloc(L->a, (size_t)nc * sizeof(uint32_t));
+        if (!na) return -1;
+        L->a = na;
+        L->cap = nc;
+    }
+    int64_t p = L->len; /* sorted position by arrival */
+    while (p > 0 && L->a[p - 1] > a) {
+        L->s[p] = L->s[p - 1];
+        L->a[p] = L->a[p - 1];
+        --p;
+    }
+    L->s[p] = d;
+    L->a[p] = a;
+    ++L->len;
+    return 1;
+}
+
+int oracle_shortest_duration(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                             const uint32_t *lam, const uint32_t *perm, int32_t s, uint32_t ta, uint32_t tw,
+                             int strict, uint32_t *out) {
+    if (check_common(n, m, src, dst, t, lam, perm, s, ta, tw, out)) return -1;
+    pair_list *P = (pair_list *)calloc((size_t)n, sizeof(pair_list));
+    uint64_t *best = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    int rc = 0;
+    if (!P || !best) {
+        rc = -1;
+        goto done;
+    }
+    for (int64_t v = 0; v < n; ++v) best[v] = UINT64_MAX;
+    best[s] = 0;
+    int64_t k = 0;
+    while (k < m && t[perm[k]] < ta) ++k; /* edges departing before the window */
+    while (k < m && t[perm[k]] <= tw) {
+        uint32_t now = t[perm[k]];
+        int64_t end = k;
+        while (end < m && t[perm[end]] == now) ++end;
+        int again = 1;
+        while (again) {
+            again = 0;
+            for (int64_t j = k; j < end; ++j) {
+                uint32_t e = perm[j];
+                uint64_t arrive = (uint64_t)now + lam[e];
+                if (arrive > tw) continue; /* leaves the window */
+                int32_t u = src[e], v = dst[e];
+                if (v == s) continue; /* nothing beats sd[s] = 0 or a fresh start */
+                uint64_t base;
+                if (u == s) {
+                    base = 0;
+                } else {
+                    const pair_list *L = &P[u];
+                    int64_t i = L->len - 1; /* latest arrival in time = smallest total */
+                    while (i >= 0 && (strict ? !(L->a[i] < now) : !(L->a[i] <= now))) --i;
+                    if (i < 0) continue;
+                    base = L->s[i];
+                }
+                uint64_t total = base + lam[e];
+                if (total > 0xFFFFFFFEu) continue; /* beyond any label (cannot happen for usable edges) */
+                int ch = dpairs_insert(&P[v], (uint32_t)total, (uint32_t)arrive);
+                if (ch < 0) {
+                    rc = -1;
+                    goto done;
+                }
+                if (ch) {
+                    if (total < best[v]) best[v] = total;
+                    again = 1;
                 }
             }
         }

@@ -12,7 +12,7 @@ import pytest
 import oracle
 import synth
 from oracle import (C_MIRROR, UNREACHED, Oracle, brute_earliest_arrival, brute_fastest,
-                    brute_latest_departure, certify_ea, mirror_edges)
+                    brute_latest_departure, brute_shortest_duration, certify_ea, mirror_edges)
 from synth import EA, LD, Query
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -49,6 +49,12 @@ def test_hand_worked_example():
         got = orc.fastest(c["vertex"], c["ta"], c["tw"], c["strict"])
         assert got.tolist() == c["expect"], c
         brute = brute_fastest(el.n, el.src, el.dst, el.t, el.lam, c["vertex"], c["ta"], c["tw"], c["strict"])
+        assert brute.tolist() == c["expect"], c
+    for c in g["shortest_duration_cases"]:
+        got = orc.shortest_duration(c["vertex"], c["ta"], c["tw"], c["strict"])
+        assert got.tolist() == c["expect"], c
+        brute = brute_shortest_duration(el.n, el.src, el.dst, el.t, el.lam, c["vertex"], c["ta"], c["tw"],
+                                        c["strict"])
         assert brute.tolist() == c["expect"], c
 
 
@@ -301,3 +307,68 @@ def test_fastest_invariants(tiny_workload, strict):
         assert np.array_equal(fp != UNREACHED, reached)
         assert np.all(fp[reached] <= ea[reached] - ta)
         assert np.all(fp[reached] <= tw - ta)
+
+
+# ---- shortest duration ----------------------------------------------------------------
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_shortest_duration_brute_force_tiny_graphs(strict):
+    """The one-pass (total, arrival) pair scan against enumeration of simple paths."""
+    for el, v, ta, tw in _tiny_cases(1500):
+        got = Oracle(el).shortest_duration(v, ta, tw, strict)
+        want = brute_shortest_duration(el.n, el.src, el.dst, el.t, el.lam, v, ta, tw, strict)
+        assert np.array_equal(got, want), (el.src, el.dst, el.t, el.lam, v, ta, tw)
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_shortest_duration_reduces_to_dijkstra(strict):
+    """A static weighted graph whose every edge is present at each integer time 0..H (waiting
+    is free and H exceeds every path's length): the least total duration is the static
+    shortest-path distance (scipy's Dijkstra), under either predicate (durations >= 1)."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import dijkstra
+    for seed in range(6):
+        n = 40
+        st = synth.random_small(n, 100, 0x7600 + seed, t_max=0, lam_max=5, lam_min=1)
+        H = 5 * n + 5
+        rows = [(int(u), int(v), tt, int(l)) for u, v, l in zip(st.src, st.dst, st.lam) for tt in range(H + 1)]
+        el = from_rows(n, rows)
+        s = seed
+        got = Oracle(el).shortest_duration(s, 0, 2 * H, strict)
+        w = {}
+        for u, v, l in zip(st.src, st.dst, st.lam):  # parallel edges: the lightest counts
+            if u != v:
+                w[(int(u), int(v))] = min(w.get((int(u), int(v)), 99), int(l))
+        M = csr_matrix(([x for x in w.values()], ([k[0] for k in w], [k[1] for k in w])), shape=(n, n))
+        dist = dijkstra(M, indices=s)
+        want = [0 if v == s else (UNREACHED if np.isinf(dist[v]) else int(dist[v])) for v in range(n)]
+        assert got.tolist() == want, seed
+
+
+def test_shortest_duration_reductions_and_invariants(tiny_workload):
+    """(1) All edges at t = 0 with zero duration: 0 exactly on the BFS-reachable set.
+    (2) On the 10^5-edge graph: sd <= fp (waiting only adds to a path's duration), sd is
+    finite exactly where earliest arrival is, and sd[v] >= the smallest duration of v's
+    usable in-edges."""
+    for seed in range(10):
+        el = synth.random_small(40, 90, 0x7700 + seed, t_max=0, lam_max=0)
+        s = seed % 40
+        got = Oracle(el).shortest_duration(s, 0, 5)
+        dist = _bfs(el.n, el.src, el.dst, s)
+        assert [g == 0 for g in got] == [d >= 0 for d in dist]
+    el, orc = tiny_workload
+    for s in (3, 99, 1234):
+        for strict in (0, 1):
+            ta, tw = 1 << 17, (1 << 20) - 1
+            sd = orc.shortest_duration(s, ta, tw, strict).astype(np.int64)
+            fp = orc.fastest(s, ta, tw, strict).astype(np.int64)
+            ea = orc.earliest_arrival(s, ta, tw, strict)
+            reached = ea != UNREACHED
+            assert np.array_equal(sd != UNREACHED, reached)
+            assert np.all(sd[reached] <= fp[reached])
+            usable = (el.t >= ta) & (el.t.astype(np.int64) + el.lam <= tw)
+            minin = np.full(el.n, np.iinfo(np.int64).max)
+            np.minimum.at(minin, el.dst[usable], el.lam[usable].astype(np.int64))
+            others = reached.copy()
+            others[s] = False
+            assert np.all(sd[others] >= minin[others])
