@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-fastest", action="store_true")
+    p.add_argument("--no-duration", action="store_true")
     p.add_argument("--fastest-queries", type=int, default=16)
     p.add_argument("--serve-rates", default="1000,4000,16000")
     p.add_argument("--serve-queries", type=int, default=400)
@@ -282,6 +283,30 @@ def measure_fastest(torch, kx, g, el, ta, tw, count):
             "lanes": g.tuning().lanes, "sources_list": srcs[:4]}
 
 
+def measure_duration(torch, kx, g, el, ta, tw, count):
+    """Shortest-duration queries (kairos_shortest_duration) from `count` seeded sources with an
+    out-edge, window [ta, tw], device output; the first call's one-time reverse-slot build is
+    timed separately."""
+    srcs = synth.pick_vertices(el, count, 0x5D57, True, False)
+    out = torch.empty(el.n, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.shortest_duration(srcs[0], ta, tw, out)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    rounds = examined = 0
+    t0 = time.perf_counter()
+    for s in srcs:
+        st = g.shortest_duration(s, ta, tw, out)
+        rounds += st.rounds
+        examined += st.examined_edges
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"queries": count, "queries_per_s": count / dt, "ms_per_query": dt * 1e3 / count,
+            "rounds_per_query": rounds / count, "examined_edges_per_s": examined / dt,
+            "first_call_ms": first_s * 1e3, "window": [int(ta), int(tw)], "sources": "0x5D57 draw"}
+
+
 def replica_reduce(step_ms, te_step, world, device):
     """Across replicas: the slowest rank's step time and the total traversed edges.  Replicas
     hold the whole graph and answer their own query shard, so this is the only exchange."""
@@ -296,7 +321,7 @@ def replica_reduce(step_ms, te_step, world, device):
     return float(t.item()), int(e.item())
 
 
-def cpu_baseline(el, queries, budget_s=20.0, fastest=None):
+def cpu_baseline(el, queries, budget_s=20.0, fastest=None, duration=None):
     """The oracle as it stands, single-threaded on a host core, on a bounded sample.  With
     `fastest` (the GPU fastest-path measurement), also the oracle's fastest-path pair scan
     on its first sources (up to about 10 s)."""
@@ -337,7 +362,22 @@ def cpu_baseline(el, queries, budget_s=20.0, fastest=None):
                 break
         fast = {"queries_per_s": f_n / f_s, "sample": f"{f_n} of the {fastest['queries']} fastest-path sources, "
                                                       f"one-pass pair scan on 1 host core"}
-    return {"fastest": fast, "value": te / scan_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    sdur = None
+    if duration:
+        ta, tw = duration["window"]
+        srcs = synth.pick_vertices(el, duration["queries"], 0x5D57, True, False)
+        d_s, d_n = 0.0, 0
+        for s in srcs:
+            t1 = time.perf_counter()
+            orc.shortest_duration(s, ta, tw, 0)
+            d_s += time.perf_counter() - t1
+            d_n += 1
+            if d_s > budget_s / 2:
+                break
+        sdur = {"queries_per_s": d_n / d_s, "sample": f"{d_n} of the {duration['queries']} shortest-duration "
+                                                      f"sources, one-pass pair scan on 1 host core"}
+    return {"fastest": fast, "shortest_duration": sdur, "value": te / scan_s / 1e9, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
             "sample": f"{len(done)} runs over {len(queries)} queries ({sum(queries[i].kind == 0 for i in done)} EA, "
                       f"{sum(queries[i].kind == 1 for i in done)} LD), one-pass scans on 1 host core; "
                       f"time-order sort ({sort_s:.1f} s) excluded as preprocessing",
@@ -517,13 +557,16 @@ def main():
         fastest = None
         if not args.no_fastest:
             fastest = measure_fastest(torch, kx, g, el, queries[0].ta, queries[0].tw, args.fastest_queries)
+        duration = None
+        if not args.no_duration:
+            duration = measure_duration(torch, kx, g, el, queries[0].ta, queries[0].tw, args.fastest_queries)
         g.close()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    cpu = None if args.no_cpu else cpu_baseline(el, queries, fastest=fastest)
+    cpu = None if args.no_cpu else cpu_baseline(el, queries, fastest=fastest, duration=duration)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -549,6 +592,7 @@ def main():
                      "algorithmic_bytes_per_step": bytes_step},
         "served": served,
         "fastest": fastest,
+        "shortest_duration": duration,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * n_launch,

@@ -200,6 +200,26 @@ typedef struct {
 kairos_status kairos_fastest_path(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, int32_t strict,
                                   uint32_t *out, kairos_fastest_stats *stats);
 
+/* Shortest durations from src within [ta, tw] (Sec. 2.3 names shortest paths among the
+ * minimal temporal paths; the definition is that of the paper's reference on temporal path
+ * problems): out[v] = the minimum over time-respecting paths P from src to v inside the
+ * window of the sum of P's edge durations (waiting is free); out[src] = 0;
+ * KAIROS_UNREACHED otherwise.  strict: 0 Succeeds, 1 StrictlySucceeds.
+ * Method: label-correcting rounds over edge labels D(e) = lambda_e + f_u(t_e), where f_u(tau)
+ * is the least label of u's in-edges arriving by tau, kept as suffix minima over u's in-edges
+ * in the reversed graph's order; at most n rounds.  The first call builds the reverse-slot
+ * map of the edges (one radix sort) and three per-edge uint32 arrays, kept with the graph.
+ * Needs the reverse graph (not built with skip_reverse: INVALID_ARG).  out: uint32_t[n], host
+ * or device.  stats (may be NULL): rounds and usable edges examined.  Synchronous.
+ * Errors: INVALID_ARG, TIMEOUT (round cap), OOM, CUDA. */
+typedef struct {
+    uint64_t rounds;          /* relaxation rounds run */
+    uint64_t examined_edges;  /* usable out-edges of active vertices, summed over the rounds */
+} kairos_duration_stats;
+
+kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, int32_t strict,
+                                       uint32_t *out, kairos_duration_stats *stats);
+
 /* ---- launch shape ----------------------------------------------------------------- */
 
 kairos_status kairos_get_tuning(const kairos_graph *g, kairos_tuning *t);

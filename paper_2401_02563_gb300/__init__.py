@@ -93,6 +93,10 @@ class kairos_fastest_stats(ctypes.Structure):
     _fields_ = [("start_times", ctypes.c_uint64), ("launches", ctypes.c_uint64), ("relaxed_edges", ctypes.c_uint64)]
 
 
+class kairos_duration_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint64), ("examined_edges", ctypes.c_uint64)]
+
+
 # Every function the header declares, with its ctypes signature.
 SIGNATURES = {
     "kairos_graph_build": (ctypes.c_int, [ctypes.POINTER(kairos_edge_list), ctypes.POINTER(kairos_graph_opts),
@@ -106,6 +110,8 @@ SIGNATURES = {
                                           ctypes.POINTER(kairos_query_stats)]),
     "kairos_fastest_path": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32, _P,
                                            ctypes.POINTER(kairos_fastest_stats)]),
+    "kairos_shortest_duration": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
+                                                ctypes.c_int32, _P, ctypes.POINTER(kairos_duration_stats)]),
     "kairos_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
     "kairos_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
     "kairos_autotune": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32,
@@ -286,6 +292,16 @@ def kairos_fastest_path(g, n, src, ta, tw, out, strict=0, want_stats=False):
     return st
 
 
+def kairos_shortest_duration(g, n, src, ta, tw, out, strict=0):
+    """Shortest-duration labels from src into out (uint32[n], host or device); returns the
+    kairos_duration_stats."""
+    _check_out(out, n)
+    st = kairos_duration_stats()
+    _check(lib().kairos_shortest_duration(g, int(src), int(ta), int(tw), int(strict), _ptr(out), ctypes.byref(st)),
+           "kairos_shortest_duration")
+    return st
+
+
 def kairos_earliest_arrival_noalloc(g, n, src, ta, tw, out):
     """Earliest arrival that allocates no device memory; out must be a CUDA tensor."""
     _check_out(out, n)
@@ -433,6 +449,9 @@ class Graph:
 
     def fastest_path(self, src, ta, tw, out, strict=0, want_stats=False):
         return kairos_fastest_path(self.handle, self.n, src, ta, tw, out, strict, want_stats)
+
+    def shortest_duration(self, src, ta, tw, out, strict=0):
+        return kairos_shortest_duration(self.handle, self.n, src, ta, tw, out, strict)
 
     def batch(self, queries, out, want_stats=True):
         return kairos_batch_query(self.handle, self.n, queries, out, want_stats)

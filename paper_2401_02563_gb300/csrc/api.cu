@@ -543,6 +543,7 @@ void kairos_graph_free(kairos_graph *g) {
         cudaGetLastError();
         release_work_arrays(g);
         release_fastest_scratch(g);
+        release_duration_scratch(g);
         free_csr(g->A, &g->fwd);
         free_csr(g->A, &g->rev);
         if (g->work.ctr_host) cudaFreeHost(g->work.ctr_host);

@@ -276,6 +276,24 @@ int grid_for(int64_t items, int threads) {
     return (int)std::min<int64_t>(g, 65535LL * 16);
 }
 
+// src_of[i] = the vertex whose forward list holds position i (binary search over offsets).
+__global__ void edge_sources(int64_t n, int64_t m, const uint64_t *off, int32_t *src_of) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n;  // last u with off[u] <= i
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (off[mid] <= (uint64_t)i) lo = mid; else hi = mid;
+        }
+        src_of[i] = (int32_t)lo;
+    }
+}
+
+// slot[vals[j]] = j: the inverse of the sorted payload.
+__global__ void invert_payload(int64_t m, const uint32_t *vals, uint32_t *slot) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        slot[vals[j]] = (uint32_t)j;
+}
+
 }  // namespace
 
 kairos_status validate_edges(cudaStream_t s, int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
@@ -396,6 +414,65 @@ kairos_status build_csr(const Allocator &A, cudaStream_t s, int64_t n, int64_t m
     }
     c.max_deg = (int64_t)h[2];
     *out = c;
+    return KAIROS_OK;
+}
+
+kairos_status build_reverse_slots(const Allocator &A, cudaStream_t s, int64_t n, int64_t m, const Csr &fwd,
+                                  int lam_bits, uint32_t *fwd2rev) {
+    if (m <= 0) return KAIROS_OK;
+    const int64_t nb = std::max<int64_t>(cdiv(m, RS_TILE), 1);
+    const int64_t hist_n = 256 * nb;
+    int32_t *src_of = (int32_t *)A.get((size_t)m * 4);
+    uint64_t *k0 = (uint64_t *)A.get((size_t)m * 8);
+    uint64_t *k1 = (uint64_t *)A.get((size_t)m * 8);
+    uint32_t *v0 = (uint32_t *)A.get((size_t)m * 4);
+    uint32_t *v1 = (uint32_t *)A.get((size_t)m * 4);
+    uint32_t *hist = (uint32_t *)A.get((size_t)hist_n * 4);
+    uint32_t *offs = (uint32_t *)A.get((size_t)hist_n * 4);
+    uint32_t *tmp = (uint32_t *)A.get((size_t)scan_tmp_words(hist_n) * 4);
+    auto release_tmp = [&]() {
+        A.put(src_of); A.put(k0); A.put(k1); A.put(v0); A.put(v1); A.put(hist); A.put(offs); A.put(tmp);
+    };
+    if (!src_of || !k0 || !k1 || !v0 || !v1 || !hist || !offs || !tmp) {
+        release_tmp();
+        return fail(KAIROS_ERR_OOM, "reverse slots: device allocation failed");
+    }
+    const int g = grid_for(m, 256);
+    edge_sources<<<g, 256, 0, s>>>(n, m, fwd.off, src_of);
+    cudaError_t e = cudaGetLastError();
+    // keys of the reversed, time-mirrored edges (head << 32 | TMAX - (t + lam)), payload the
+    // forward position: sorted exactly as the reverse list (ties in forward order)
+    if (e == cudaSuccess) {
+        if (lam_bits == 16)
+            make_keys<uint16_t><<<g, 256, 0, s>>>(m, src_of, fwd.dst, fwd.t, (const uint16_t *)fwd.lam, 1, k0, v0);
+        else
+            make_keys<uint32_t><<<g, 256, 0, s>>>(m, src_of, fwd.dst, fwd.t, (const uint32_t *)fwd.lam, 1, k0, v0);
+        e = cudaGetLastError();
+    }
+    int vbits = 0;
+    while (vbits < 63 && (1LL << vbits) < n) ++vbits;
+    const int passes = (32 + vbits + 7) / 8;
+    uint64_t *ki = k0, *ko = k1;
+    uint32_t *vi = v0, *vo = v1;
+    for (int p = 0; p < passes && e == cudaSuccess; ++p) {
+        const int shift = 8 * p;
+        rs_upsweep<<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, m, shift, hist, nb);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = excl_scan(hist, offs, hist_n, tmp, s);
+        if (e == cudaSuccess) {
+            rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, vi, ko, vo, m, shift, offs, nb);
+            e = cudaGetLastError();
+        }
+        std::swap(ki, ko);
+        std::swap(vi, vo);
+    }
+    if (e == cudaSuccess) {
+        invert_payload<<<g, 256, 0, s>>>(m, vi, fwd2rev);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    release_tmp();
+    if (e != cudaSuccess) return cuda_fail(e, "reverse slots");
     return KAIROS_OK;
 }
 

@@ -183,6 +183,12 @@ kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_
                                  kairos_query_stats *stats, int lanes);
 // Free the fastest-path scratch of a graph (fastest.cu).
 void release_fastest_scratch(kairos_graph *g);
+// Free the shortest-duration state of a graph (duration.cu).
+void release_duration_scratch(kairos_graph *g);
+// fwd2rev[i] = the slot of forward edge i in the reverse list's order (per head by mirrored
+// time TMAX - (t + lam), i.e. latest arrival first; ties in forward order).
+kairos_status build_reverse_slots(const Allocator &A, cudaStream_t s, int64_t n, int64_t m, const Csr &fwd,
+                                  int lam_bits, uint32_t *fwd2rev);
 
 // ---- device build ------------------------------------------------------------------------
 
@@ -245,6 +251,11 @@ struct kairos_graph {
         // (host outputs) and the start times of the pass
         uint32_t *fast_rows = nullptr, *fast_best = nullptr, *fast_d = nullptr;
         int64_t fast_rows_cap = 0;
+        // shortest durations: reverse slot of every forward edge, per-slot edge labels and
+        // their per-head suffix minima, per-vertex flags, round counters
+        uint32_t *sd_slot = nullptr, *sd_d = nullptr, *sd_sm = nullptr;
+        uint8_t *sd_changed = nullptr, *sd_active = nullptr;
+        unsigned long long *sd_ctr = nullptr, *sd_ctr_host = nullptr;
     } work;
     int last_launches = 0;
     int64_t graph_launches = 0;

@@ -1,0 +1,268 @@
+// Shortest durations (least total travel time; the "shortest path" among the minimal temporal
+// paths of Sec. 2.3) as a label-correcting computation over edge labels.
+//
+// For a usable edge e = (u, v, t, lam) let D(e) be the least total duration of a
+// time-respecting path from the source that ends with e, and let
+//     f_u(tau) = min { D(e') : e' enters u and arrives by tau (before tau under
+//                      StrictlySucceeds) },   f_src = 0 for every departure in the window.
+// Then D(e) = lam + f_u(t) and the answer at v != src is the minimum D over v's in-edges.
+// Every round relaxes the out-edges of the vertices whose f changed, and then recomputes
+// f for the heads whose in-edge labels dropped.  f_u is a suffix minimum over u's in-edges
+// in the reversed graph's order (latest arrival first), so one binary search over the
+// reversed list's mirrored times finds the in-edges that arrive in time.  Labels only fall,
+// and after k rounds every path of k edges is accounted for; simple paths suffice, so at
+// most n rounds.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace kairos {
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__global__ void sd_init_kernel(int64_t m, int64_t n, uint32_t *d, uint32_t *sm, uint8_t *changed, uint8_t *active,
+                               int32_t src) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        d[i] = INF;
+        sm[i] = INF;
+    }
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        changed[v] = 0;
+        active[v] = (v == src);
+    }
+}
+
+// Relax the usable out-edges of every active vertex: D(e) = min(D(e), lam + f_u(t)).  A warp
+// takes 32 vertices, then each of the active ones in turn with its lanes over the edges.
+// ctr[0]: set when some label dropped; ctr[1]: edges examined.
+template <typename LamT>
+__global__ void sd_relax_kernel(int64_t n, const uint64_t *__restrict__ off, const int32_t *__restrict__ dst,
+                                const uint32_t *__restrict__ t, const LamT *__restrict__ lam,
+                                const uint64_t *__restrict__ roff, const uint32_t *__restrict__ rt,
+                                const uint32_t *__restrict__ slot, uint32_t *d, const uint32_t *__restrict__ sm,
+                                uint8_t *changed, uint8_t *active, int32_t src, uint32_t ta, uint32_t tw, int strict,
+                                unsigned long long *ctr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long examined = 0;
+    bool dropped = false;
+    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const int64_t v0 = base + lane;
+        const bool on = v0 < n && active[v0];
+        unsigned todo = __ballot_sync(FULL, on);
+        if (on) active[v0] = 0;
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int32_t u = (int32_t)(base + k);
+            const uint64_t e0 = off[u], e1 = off[u + 1];
+            const uint64_t r0 = roff[u], r1 = roff[u + 1];
+            for (uint64_t i = e0 + lane; i < e1; i += 32) {
+                const uint32_t ti = t[i];
+                const uint32_t li = (uint32_t)lam[i];
+                if (ti < ta || (uint64_t)ti + li > tw) continue;
+                ++examined;
+                uint32_t b;
+                if (u == src) {
+                    b = 0;
+                } else {
+                    // in-edges arriving by ti: mirrored time >= TMAX - ti (> under strict), a suffix
+                    const uint32_t key = TMAX - ti;
+                    uint64_t lo = r0, hi = r1;
+                    while (lo < hi) {
+                        const uint64_t mid = (lo + hi) >> 1;
+                        const bool below = strict ? (rt[mid] <= key) : (rt[mid] < key);
+                        if (below) lo = mid + 1; else hi = mid;
+                    }
+                    b = lo < r1 ? sm[lo] : INF;
+                }
+                if (b == INF) continue;
+                const uint32_t cand = b + li;  // a path's total duration: at most tw - ta
+                const uint32_t j = slot[i];
+                if (cand < d[j]) {  // the label may be stale (never below the current one)
+                    atomicMin(&d[j], cand);
+                    changed[dst[i]] = 1;
+                    dropped = true;
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) examined += __shfl_xor_sync(FULL, examined, o);
+    const bool any = __any_sync(FULL, dropped);
+    if (lane == 0) {
+        if (examined) atomicAdd(&ctr[1], examined);
+        if (any) atomicExch(&ctr[0], 1ull);
+    }
+}
+
+// Recompute the suffix minima of the in-edge labels of every changed vertex (latest arrival
+// first, so the suffix from a slot covers the in-edges arriving no later); it becomes active.
+__global__ void sd_suffix_kernel(int64_t n, const uint64_t *__restrict__ roff, const uint32_t *d, uint32_t *sm,
+                                 uint8_t *changed, uint8_t *active) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const int64_t v0 = base + lane;
+        const bool on = v0 < n && changed[v0];
+        unsigned todo = __ballot_sync(FULL, on);
+        if (on) {
+            changed[v0] = 0;
+            active[v0] = 1;
+        }
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t v = base + k;
+            const int64_t b = (int64_t)roff[v], e = (int64_t)roff[v + 1];
+            uint32_t carry = INF;
+            for (int64_t cb = e; cb > b; cb -= 32) {
+                const int64_t j = cb - 32 + lane;
+                uint32_t x = j >= b ? d[j] : INF;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_down_sync(FULL, x, o);
+                    if (lane + o < 32) x = min(x, y);
+                }
+                x = min(x, carry);
+                if (j >= b) sm[j] = x;
+                carry = __shfl_sync(FULL, x, 0);
+            }
+        }
+    }
+}
+
+__global__ void sd_result_kernel(int64_t n, const uint64_t *__restrict__ roff, const uint32_t *__restrict__ sm,
+                                 int32_t src, uint32_t *out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = (v == src) ? 0u : (roff[v] < roff[v + 1] ? sm[roff[v]] : INF);
+}
+
+bool on_device(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+kairos_status ensure_duration_state(kairos_graph *g) {
+    auto &w = g->work;
+    if (w.sd_slot) return KAIROS_OK;
+    const int64_t n = g->n, m = std::max<int64_t>(g->m, 1);
+    const auto &A = g->A;
+    w.sd_slot = (uint32_t *)A.get((size_t)m * 4);
+    w.sd_d = (uint32_t *)A.get((size_t)m * 4);
+    w.sd_sm = (uint32_t *)A.get((size_t)m * 4);
+    w.sd_changed = (uint8_t *)A.get((size_t)n);
+    w.sd_active = (uint8_t *)A.get((size_t)n);
+    w.sd_ctr = (unsigned long long *)A.get(2 * sizeof(unsigned long long));
+    cudaError_t e = cudaMallocHost(&w.sd_ctr_host, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        w.sd_ctr_host = nullptr;
+    }
+    if (!w.sd_slot || !w.sd_d || !w.sd_sm || !w.sd_changed || !w.sd_active || !w.sd_ctr || !w.sd_ctr_host) {
+        release_duration_scratch(g);
+        return fail(KAIROS_ERR_OOM, "shortest duration: device allocation failed");
+    }
+    kairos_status st = build_reverse_slots(A, g->stream, n, g->m, g->fwd, g->lam_bits, w.sd_slot);
+    if (st != KAIROS_OK) release_duration_scratch(g);
+    return st;
+}
+
+}  // namespace
+
+void release_duration_scratch(kairos_graph *g) {
+    auto &w = g->work;
+    const auto &A = g->A;
+    A.put(w.sd_slot);
+    A.put(w.sd_d);
+    A.put(w.sd_sm);
+    A.put(w.sd_changed);
+    A.put(w.sd_active);
+    A.put(w.sd_ctr);
+    if (w.sd_ctr_host) cudaFreeHost(w.sd_ctr_host);
+    w.sd_slot = w.sd_d = w.sd_sm = nullptr;
+    w.sd_changed = w.sd_active = nullptr;
+    w.sd_ctr = w.sd_ctr_host = nullptr;
+}
+
+}  // namespace kairos
+
+using namespace kairos;
+
+extern "C" kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw,
+                                                  int32_t strict, uint32_t *out, kairos_duration_stats *stats) {
+    if (!g || !out) return fail(KAIROS_ERR_INVALID_ARG, "shortest duration: NULL argument");
+    if (src < 0 || (int64_t)src >= g->n) return fail(KAIROS_ERR_INVALID_ARG, "shortest duration: source out of range");
+    if (ta > tw || tw > TMAX) return fail(KAIROS_ERR_INVALID_ARG, "shortest duration: need ta <= tw <= KAIROS_TIME_MAX");
+    if (strict != 0 && strict != 1) return fail(KAIROS_ERR_INVALID_ARG, "shortest duration: strict is 0 or 1");
+    if (!g->has_rev)
+        return fail(KAIROS_ERR_INVALID_ARG, "shortest duration: the graph was built without its reverse (skip_reverse)");
+    std::lock_guard<std::mutex> lk(g->mu);
+    kairos_status st = ensure_duration_state(g);
+    if (st != KAIROS_OK) return st;
+    auto &w = g->work;
+    cudaStream_t s = g->stream;
+    const int64_t n = g->n, m = g->m;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((std::max(n, m) + 255) / 256, (int64_t)g->sm_count * 16));
+    const int vgrid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->sm_count * 16));
+    KAIROS_CUDA(cudaEventRecord(w.ev0, s), "event record");
+    sd_init_kernel<<<grid, 256, 0, s>>>(m, n, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active, src);
+    KAIROS_CUDA(cudaGetLastError(), "shortest duration: init");
+    KAIROS_CUDA(cudaMemsetAsync(w.sd_ctr, 0, 2 * sizeof(unsigned long long), s), "shortest duration: counters");
+    uint64_t rounds = 0;
+    const uint64_t cap = (uint64_t)n + 1;
+    for (;;) {
+        if (rounds >= cap) return fail(KAIROS_ERR_TIMEOUT, "shortest duration: round cap (n + 1) reached");
+        ++rounds;
+        KAIROS_CUDA(cudaMemsetAsync(w.sd_ctr, 0, sizeof(unsigned long long), s), "shortest duration: flag");
+        if (g->lam_bits == 16)
+            sd_relax_kernel<uint16_t><<<vgrid, 256, 0, s>>>(n, g->fwd.off, g->fwd.dst, g->fwd.t,
+                                                            (const uint16_t *)g->fwd.lam, g->rev.off, g->rev.t,
+                                                            w.sd_slot, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active,
+                                                            src, ta, tw, strict, w.sd_ctr);
+        else
+            sd_relax_kernel<uint32_t><<<vgrid, 256, 0, s>>>(n, g->fwd.off, g->fwd.dst, g->fwd.t,
+                                                            (const uint32_t *)g->fwd.lam, g->rev.off, g->rev.t,
+                                                            w.sd_slot, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active,
+                                                            src, ta, tw, strict, w.sd_ctr);
+        KAIROS_CUDA(cudaGetLastError(), "shortest duration: relax");
+        KAIROS_CUDA(cudaMemcpyAsync(w.sd_ctr_host, w.sd_ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
+                    "shortest duration: flag");
+        KAIROS_CUDA(cudaStreamSynchronize(s), "shortest duration: round");
+        if (w.sd_ctr_host[0] == 0) break;  // no label dropped: the suffix minima are final
+        sd_suffix_kernel<<<vgrid, 256, 0, s>>>(n, g->rev.off, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active);
+        KAIROS_CUDA(cudaGetLastError(), "shortest duration: suffix minima");
+    }
+    uint32_t *res = out;
+    const bool dev = on_device(out);
+    if (!dev) {
+        res = (uint32_t *)g->A.get((size_t)n * 4);
+        if (!res) return fail(KAIROS_ERR_OOM, "shortest duration: device allocation failed");
+    }
+    sd_result_kernel<<<vgrid, 256, 0, s>>>(n, g->rev.off, w.sd_sm, src, res);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(w.ev1, s);
+    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(out, res, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (!dev) g->A.put(res);
+    if (e != cudaSuccess) return cuda_fail(e, "shortest duration: result");
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, w.ev0, w.ev1) == cudaSuccess) g->last_kernel_ms = ms;
+    cudaGetLastError();
+    if (stats) {
+        stats->rounds = rounds;
+        stats->examined_edges = w.sd_ctr_host[1];
+    }
+    return KAIROS_OK;
+}

@@ -49,7 +49,8 @@ def test_status_strings(library):
 
 
 STRUCTS = ["kairos_edge_list", "kairos_graph_opts", "kairos_query", "kairos_query_stats", "kairos_tuning",
-           "kairos_graph_info", "kairos_serve_opts", "kairos_result_info", "kairos_fastest_stats"]
+           "kairos_graph_info", "kairos_serve_opts", "kairos_result_info", "kairos_fastest_stats",
+           "kairos_duration_stats"]
 
 
 def test_binding_struct_layouts_match_the_c_compiler(tmp_path):
