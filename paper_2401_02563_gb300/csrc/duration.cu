@@ -12,6 +12,10 @@
 // reversed list's mirrored times finds the in-edges that arrive in time.  Labels only fall,
 // and after k rounds every path of k edges is accounted for; simple paths suffice, so at
 // most n rounds.
+// Work per round follows the changes: when an in-edge label of u drops, f_u changes only from
+// that edge's arrival on, so u's next relaxation starts at the first out-edge departing then
+// (its list is in departure order); and u's suffix minima are recomputed only from the
+// highest slot whose label dropped down to the start of its list.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,8 +29,11 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
+// from_cur[v]: earliest arrival whose label dropped, for v's coming relaxation; from_next[v]:
+// the same, collected during a relaxation round; hislot[v]: 1 + the highest slot of v's in-list
+// whose label dropped (0: none).
 __global__ void sd_init_kernel(int64_t m, int64_t n, uint32_t *d, uint32_t *sm, uint8_t *changed, uint8_t *active,
-                               int32_t src) {
+                               uint32_t *from_cur, uint32_t *from_next, uint32_t *hislot, int32_t src) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         d[i] = INF;
@@ -35,6 +42,9 @@ __global__ void sd_init_kernel(int64_t m, int64_t n, uint32_t *d, uint32_t *sm, 
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         changed[v] = 0;
         active[v] = (v == src);
+        from_cur[v] = (v == src) ? 0u : INF;  // the source starts paths at every departure
+        from_next[v] = INF;
+        hislot[v] = 0;
     }
 }
 
@@ -46,8 +56,9 @@ __global__ void sd_relax_kernel(int64_t n, const uint64_t *__restrict__ off, con
                                 const uint32_t *__restrict__ t, const LamT *__restrict__ lam,
                                 const uint64_t *__restrict__ roff, const uint32_t *__restrict__ rt,
                                 const uint32_t *__restrict__ slot, uint32_t *d, const uint32_t *__restrict__ sm,
-                                uint8_t *changed, uint8_t *active, int32_t src, uint32_t ta, uint32_t tw, int strict,
-                                unsigned long long *ctr) {
+                                uint8_t *changed, uint8_t *active, const uint32_t *__restrict__ from_cur,
+                                uint32_t *from_next, uint32_t *hislot, int32_t src, uint32_t ta, uint32_t tw,
+                                int strict, unsigned long long *ctr) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -62,8 +73,21 @@ __global__ void sd_relax_kernel(int64_t n, const uint64_t *__restrict__ off, con
             const int k = __ffs(todo) - 1;
             todo &= todo - 1;
             const int32_t u = (int32_t)(base + k);
-            const uint64_t e0 = off[u], e1 = off[u + 1];
+            uint64_t e0 = off[u];
+            const uint64_t e1 = off[u + 1];
             const uint64_t r0 = roff[u], r1 = roff[u + 1];
+            // f_u changed from arrival `from` on: skip the out-edges departing before it (at it,
+            // too, under StrictlySucceeds); departures are ascending
+            const uint32_t from = from_cur[u];
+            if (u != src) {
+                uint64_t lo = e0, hi2 = e1;
+                while (lo < hi2) {
+                    const uint64_t mid = (lo + hi2) >> 1;
+                    const bool before = strict ? (t[mid] <= from) : (t[mid] < from);
+                    if (before) lo = mid + 1; else hi2 = mid;
+                }
+                e0 = lo;
+            }
             for (uint64_t i = e0 + lane; i < e1; i += 32) {
                 const uint32_t ti = t[i];
                 const uint32_t li = (uint32_t)lam[i];
@@ -87,8 +111,11 @@ __global__ void sd_relax_kernel(int64_t n, const uint64_t *__restrict__ off, con
                 const uint32_t cand = b + li;  // a path's total duration: at most tw - ta
                 const uint32_t j = slot[i];
                 if (cand < d[j]) {  // the label may be stale (never below the current one)
+                    const int32_t v = dst[i];
                     atomicMin(&d[j], cand);
-                    changed[dst[i]] = 1;
+                    atomicMin(&from_next[v], ti + li);
+                    atomicMax(&hislot[v], j + 1u);
+                    changed[v] = 1;
                     dropped = true;
                 }
             }
@@ -105,7 +132,8 @@ __global__ void sd_relax_kernel(int64_t n, const uint64_t *__restrict__ off, con
 // Recompute the suffix minima of the in-edge labels of every changed vertex (latest arrival
 // first, so the suffix from a slot covers the in-edges arriving no later); it becomes active.
 __global__ void sd_suffix_kernel(int64_t n, const uint64_t *__restrict__ roff, const uint32_t *d, uint32_t *sm,
-                                 uint8_t *changed, uint8_t *active) {
+                                 uint8_t *changed, uint8_t *active, uint32_t *from_cur, uint32_t *from_next,
+                                 uint32_t *hislot) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -113,16 +141,23 @@ __global__ void sd_suffix_kernel(int64_t n, const uint64_t *__restrict__ roff, c
         const int64_t v0 = base + lane;
         const bool on = v0 < n && changed[v0];
         unsigned todo = __ballot_sync(FULL, on);
+        uint32_t top = 0;
         if (on) {
             changed[v0] = 0;
             active[v0] = 1;
+            from_cur[v0] = from_next[v0];
+            from_next[v0] = INF;
+            top = hislot[v0];
+            hislot[v0] = 0;
         }
         while (todo) {
             const int k = __ffs(todo) - 1;
             todo &= todo - 1;
             const int64_t v = base + k;
-            const int64_t b = (int64_t)roff[v], e = (int64_t)roff[v + 1];
-            uint32_t carry = INF;
+            const int64_t b = (int64_t)roff[v];
+            // slots above the highest dropped one keep their labels and suffix minima
+            const int64_t e = (int64_t)__shfl_sync(FULL, top, k);
+            uint32_t carry = (e < (int64_t)roff[v + 1]) ? sm[e] : INF;
             for (int64_t cb = e; cb > b; cb -= 32) {
                 const int64_t j = cb - 32 + lane;
                 uint32_t x = j >= b ? d[j] : INF;
@@ -164,13 +199,15 @@ kairos_status ensure_duration_state(kairos_graph *g) {
     w.sd_sm = (uint32_t *)A.get((size_t)m * 4);
     w.sd_changed = (uint8_t *)A.get((size_t)n);
     w.sd_active = (uint8_t *)A.get((size_t)n);
+    w.sd_from = (uint32_t *)A.get((size_t)n * 3 * 4);  // from_cur, from_next, hi
     w.sd_ctr = (unsigned long long *)A.get(2 * sizeof(unsigned long long));
     cudaError_t e = cudaMallocHost(&w.sd_ctr_host, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaGetLastError();
         w.sd_ctr_host = nullptr;
     }
-    if (!w.sd_slot || !w.sd_d || !w.sd_sm || !w.sd_changed || !w.sd_active || !w.sd_ctr || !w.sd_ctr_host) {
+    if (!w.sd_slot || !w.sd_d || !w.sd_sm || !w.sd_changed || !w.sd_active || !w.sd_from || !w.sd_ctr ||
+        !w.sd_ctr_host) {
         release_duration_scratch(g);
         return fail(KAIROS_ERR_OOM, "shortest duration: device allocation failed");
     }
@@ -189,10 +226,12 @@ void release_duration_scratch(kairos_graph *g) {
     A.put(w.sd_sm);
     A.put(w.sd_changed);
     A.put(w.sd_active);
+    A.put(w.sd_from);
     A.put(w.sd_ctr);
     if (w.sd_ctr_host) cudaFreeHost(w.sd_ctr_host);
     w.sd_slot = w.sd_d = w.sd_sm = nullptr;
     w.sd_changed = w.sd_active = nullptr;
+    w.sd_from = nullptr;
     w.sd_ctr = w.sd_ctr_host = nullptr;
 }
 
@@ -217,7 +256,9 @@ extern "C" kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, 
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((std::max(n, m) + 255) / 256, (int64_t)g->sm_count * 16));
     const int vgrid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->sm_count * 16));
     KAIROS_CUDA(cudaEventRecord(w.ev0, s), "event record");
-    sd_init_kernel<<<grid, 256, 0, s>>>(m, n, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active, src);
+    uint32_t *from_cur = w.sd_from, *from_next = w.sd_from + n, *hislot = w.sd_from + 2 * n;
+    sd_init_kernel<<<grid, 256, 0, s>>>(m, n, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active, from_cur, from_next,
+                                        hislot, src);
     KAIROS_CUDA(cudaGetLastError(), "shortest duration: init");
     KAIROS_CUDA(cudaMemsetAsync(w.sd_ctr, 0, 2 * sizeof(unsigned long long), s), "shortest duration: counters");
     uint64_t rounds = 0;
@@ -230,18 +271,19 @@ extern "C" kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, 
             sd_relax_kernel<uint16_t><<<vgrid, 256, 0, s>>>(n, g->fwd.off, g->fwd.dst, g->fwd.t,
                                                             (const uint16_t *)g->fwd.lam, g->rev.off, g->rev.t,
                                                             w.sd_slot, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active,
-                                                            src, ta, tw, strict, w.sd_ctr);
+                                                            from_cur, from_next, hislot, src, ta, tw, strict, w.sd_ctr);
         else
             sd_relax_kernel<uint32_t><<<vgrid, 256, 0, s>>>(n, g->fwd.off, g->fwd.dst, g->fwd.t,
                                                             (const uint32_t *)g->fwd.lam, g->rev.off, g->rev.t,
                                                             w.sd_slot, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active,
-                                                            src, ta, tw, strict, w.sd_ctr);
+                                                            from_cur, from_next, hislot, src, ta, tw, strict, w.sd_ctr);
         KAIROS_CUDA(cudaGetLastError(), "shortest duration: relax");
         KAIROS_CUDA(cudaMemcpyAsync(w.sd_ctr_host, w.sd_ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
                     "shortest duration: flag");
         KAIROS_CUDA(cudaStreamSynchronize(s), "shortest duration: round");
         if (w.sd_ctr_host[0] == 0) break;  // no label dropped: the suffix minima are final
-        sd_suffix_kernel<<<vgrid, 256, 0, s>>>(n, g->rev.off, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active);
+        sd_suffix_kernel<<<vgrid, 256, 0, s>>>(n, g->rev.off, w.sd_d, w.sd_sm, w.sd_changed, w.sd_active, from_cur,
+                                               from_next, hislot);
         KAIROS_CUDA(cudaGetLastError(), "shortest duration: suffix minima");
     }
     uint32_t *res = out;
