@@ -255,7 +255,9 @@ struct kairos_graph {
         // their per-head suffix minima, per-vertex flags, round counters
         uint32_t *sd_slot = nullptr, *sd_d = nullptr, *sd_sm = nullptr;
         uint8_t *sd_changed = nullptr, *sd_active = nullptr;
-        uint32_t *sd_from = nullptr;  // [3][n]: per-vertex change bounds (duration.cu)
+        uint32_t *sd_from = nullptr;  // [5][n] + 4: change bounds, the long-list queue, counters (duration.cu)
+        uint32_t *sd_pred[2] = {nullptr, nullptr};  // per predicate: each edge's first in-time in-list slot
+        void *sd_chunks = nullptr;                  // relaxation work items
         unsigned long long *sd_ctr = nullptr, *sd_ctr_host = nullptr;
     } work;
     int last_launches = 0;
