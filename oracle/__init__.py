@@ -1,7 +1,7 @@
 """ORACLE -- test infrastructure only.
 
 Plain CPU statement of the temporal path queries (earliest arrival, latest departure,
-fastest path, shortest duration),
+fastest path, shortest duration, temporal BFS),
 used by the test suite, the package smoke check and the CPU-baseline leg of the
 benchmark, and by nothing in the library.  `oracle.c` holds the single-threaded one-pass
 scans; this module loads it and adds pure-Python brute force over simple paths for tiny
@@ -16,8 +16,8 @@ with the source initialised to the window start):
     the first edge may depart at ta and the last may arrive at tw under either predicate;
   * EA[s] = ta; EA[v] = min arrival over paths s -> v; LD[x] = tw; LD[u] = max first
     departure over paths u -> x; FP[s] = 0; FP[v] = min (arrival - first departure) over
-    paths s -> v; SD[s] = 0; SD[v] = min sum of durations over paths s -> v;
-    unreachable = 0xFFFFFFFF.
+    paths s -> v; SD[s] = 0; SD[v] = min sum of durations over paths s -> v; temporal BFS:
+    the least number of edges of a path s -> v; unreachable = 0xFFFFFFFF.
 """
 from __future__ import annotations
 
@@ -57,7 +57,7 @@ def _load():
         L.oracle_time_order.argtypes = [ctypes.c_int64, _P, _P]
         L.oracle_time_order.restype = ctypes.c_int
         for fn in ("oracle_earliest_arrival", "oracle_latest_departure", "oracle_fastest",
-                   "oracle_shortest_duration"):
+                   "oracle_shortest_duration", "oracle_temporal_bfs"):
             f = getattr(L, fn)
             f.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int32,
                           ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _P]
@@ -133,6 +133,15 @@ class Oracle:
                                               int(strict), out.ctypes.data)
         if rc != 0:
             raise ValueError("oracle_shortest_duration: invalid arguments or allocation failure")
+        return out
+
+    def temporal_bfs(self, s: int, ta: int, tw: int, strict: int = 0) -> np.ndarray:
+        """Temporal BFS levels from s (least number of edges of a time-respecting path)."""
+        out = np.empty(self.n, np.uint32)
+        rc = _load().oracle_temporal_bfs(self.n, self.m, *self._ptrs(), int(s), int(ta), int(tw), int(strict),
+                                         out.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle_temporal_bfs: invalid arguments or allocation failure")
         return out
 
     def query(self, q) -> np.ndarray:
@@ -305,5 +314,36 @@ def brute_shortest_duration(n, src, dst, t, lam, s, ta, tw, strict=0):
             go(v, te + le, total + le, False, onpath)
             onpath.discard(v)
 
+    go(s, ta, 0, True, {s})
+    return np.array(out, np.uint32)
+
+
+def brute_temporal_bfs(n, src, dst, t, lam, s, ta, tw, strict=0):
+    """Least number of edges over vertex-simple time-respecting paths from s (a cycle cut out of
+    a time-respecting walk leaves a shorter time-respecting walk)."""
+    ones = np.ones(len(src), np.uint32)
+    out = [UNREACHED] * n
+    out[s] = 0
+    adj = [[] for _ in range(n)]
+    for e in range(len(src)):
+        adj[int(src[e])].append(e)
+
+    def go(u, arrival, hops, first, onpath):
+        for e in adj[u]:
+            te, le = int(t[e]), int(lam[e])
+            if not _usable(te, le, ta, tw):
+                continue
+            if not first and (te <= arrival if strict else te < arrival):
+                continue
+            v = int(dst[e])
+            if v in onpath:
+                continue
+            if hops + 1 < out[v]:
+                out[v] = hops + 1
+            onpath.add(v)
+            go(v, te + le, hops + 1, False, onpath)
+            onpath.discard(v)
+
+    del ones
     go(s, ta, 0, True, {s})
     return np.array(out, np.uint32)

@@ -32,6 +32,7 @@
  * Shortest duration from s (the reference's "shortest path": least total travel time):
  * sd[s] = 0, and for v != s the minimum of the sum of the edge durations over
  * time-respecting paths from s to v in the window (waiting is free); UNREACHED otherwise.
+ * Temporal BFS from s: the least number of edges of such a path (hops[s] = 0).
  *
  * Algorithm: the one-pass scan over the time-ordered edge stream of that reference
  * (credited in Sec. 7): edges are visited in ascending t (descending for latest
@@ -392,9 +393,10 @@ static int dpairs_insert(pair_list *L, uint32_t d, uint32_t a) {
     return 1;
 }
 
-int oracle_shortest_duration(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
-                             const uint32_t *lam, const uint32_t *perm, int32_t s, uint32_t ta, uint32_t tw,
-                             int strict, uint32_t *out) {
+/* cost of an edge: its duration, or 1 (unit = 1: temporal BFS, the least number of edges) */
+static int least_cost_scan(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                           const uint32_t *lam, const uint32_t *perm, int32_t s, uint32_t ta, uint32_t tw, int strict,
+                           int unit, uint32_t *out) {
     if (check_common(n, m, src, dst, t, lam, perm, s, ta, tw, out)) return -1;
     pair_list *P = (pair_list *)calloc((size_t)n, sizeof(pair_list));
     uint64_t *best = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
@@ -430,7 +432,7 @@ int oracle_shortest_duration(int64_t n, int64_t m, const int32_t *src, const int
                     if (i < 0) continue;
                     base = L->s[i];
                 }
-                uint64_t total = base + lam[e];
+                uint64_t total = base + (unit ? 1u : lam[e]);
                 if (total > 0xFFFFFFFEu) continue; /* beyond any label (cannot happen for usable edges) */
                 int ch = dpairs_insert(&P[v], (uint32_t)total, (uint32_t)arrive);
                 if (ch < 0) {
@@ -456,4 +458,21 @@ done:
     }
     free(best);
     return rc;
+}
+
+int oracle_shortest_duration(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                             const uint32_t *lam, const uint32_t *perm, int32_t s, uint32_t ta, uint32_t tw,
+                             int strict, uint32_t *out) {
+    return least_cost_scan(n, m, src, dst, t, lam, perm, s, ta, tw, strict, 0, out);
+}
+
+/*
+ * Temporal BFS from s within [ta, tw]: out[v] = the least number of edges of a
+ * time-respecting path from s to v in the window (out[s] = 0), UNREACHED otherwise.  The same
+ * pair scan as shortest durations with every edge costing 1.
+ */
+int oracle_temporal_bfs(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                        const uint32_t *lam, const uint32_t *perm, int32_t s, uint32_t ta, uint32_t tw, int strict,
+                        uint32_t *out) {
+    return least_cost_scan(n, m, src, dst, t, lam, perm, s, ta, tw, strict, 1, out);
 }

@@ -12,7 +12,8 @@ import pytest
 import oracle
 import synth
 from oracle import (C_MIRROR, UNREACHED, Oracle, brute_earliest_arrival, brute_fastest,
-                    brute_latest_departure, brute_shortest_duration, certify_ea, mirror_edges)
+                    brute_latest_departure, brute_shortest_duration, brute_temporal_bfs, certify_ea,
+                    mirror_edges)
 from synth import EA, LD, Query
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -49,6 +50,11 @@ def test_hand_worked_example():
         got = orc.fastest(c["vertex"], c["ta"], c["tw"], c["strict"])
         assert got.tolist() == c["expect"], c
         brute = brute_fastest(el.n, el.src, el.dst, el.t, el.lam, c["vertex"], c["ta"], c["tw"], c["strict"])
+        assert brute.tolist() == c["expect"], c
+    for c in g["temporal_bfs_cases"]:
+        got = orc.temporal_bfs(c["vertex"], c["ta"], c["tw"], c["strict"])
+        assert got.tolist() == c["expect"], c
+        brute = brute_temporal_bfs(el.n, el.src, el.dst, el.t, el.lam, c["vertex"], c["ta"], c["tw"], c["strict"])
         assert brute.tolist() == c["expect"], c
     for c in g["shortest_duration_cases"]:
         got = orc.shortest_duration(c["vertex"], c["ta"], c["tw"], c["strict"])
@@ -372,3 +378,36 @@ def test_shortest_duration_reductions_and_invariants(tiny_workload):
             others = reached.copy()
             others[s] = False
             assert np.all(sd[others] >= minin[others])
+
+
+# ---- temporal BFS (least number of edges) ----------------------------------------------
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_temporal_bfs_brute_force_tiny_graphs(strict):
+    for el, v, ta, tw in _tiny_cases(1500):
+        got = Oracle(el).temporal_bfs(v, ta, tw, strict)
+        want = brute_temporal_bfs(el.n, el.src, el.dst, el.t, el.lam, v, ta, tw, strict)
+        assert np.array_equal(got, want), (el.src, el.dst, el.t, el.lam, v, ta, tw)
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_temporal_bfs_reductions_and_invariants(tiny_workload, strict):
+    """(1) Every edge of a static graph present at each integer time 0..H with duration 1: the
+    level of v is its static BFS distance (H exceeds every path).  (2) On the 10^5-edge graph
+    (durations >= 1): finite exactly where earliest arrival is, and at most the shortest
+    duration (a least-duration path has at least that many edges, each lasting >= 1)."""
+    H = 70
+    for seed in range(6):
+        st = synth.random_small(30, 45, 0x7800 + seed, t_max=0, lam_max=0)
+        rows = [(int(u), int(v), tt, 1) for u, v in zip(st.src, st.dst) for tt in range(H + 1)]
+        got = Oracle(from_rows(30, rows)).temporal_bfs(seed, 0, H + 1, strict)
+        dist = _bfs(30, st.src, st.dst, seed)
+        assert got.tolist() == [UNREACHED if d < 0 else d for d in dist], seed
+    el, orc = tiny_workload
+    for s in (3, 99, 1234):
+        ta, tw = 1 << 17, (1 << 20) - 1
+        hops = orc.temporal_bfs(s, ta, tw, strict).astype(np.int64)
+        sd = orc.shortest_duration(s, ta, tw, strict).astype(np.int64)
+        reached = orc.earliest_arrival(s, ta, tw, strict) != UNREACHED
+        assert np.array_equal(hops != UNREACHED, reached)
+        assert np.all(hops[reached] <= sd[reached])
