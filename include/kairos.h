@@ -220,6 +220,14 @@ typedef struct {
 kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, int32_t strict,
                                        uint32_t *out, kairos_duration_stats *stats);
 
+/* Temporal BFS from src within [ta, tw] (Table 4's T. BFS, read over time-respecting paths; the
+ * paper gives no definition): out[v] = the least number of edges of a time-respecting path
+ * from src to v inside the window; out[src] = 0; KAIROS_UNREACHED otherwise.  The same
+ * computation as kairos_shortest_duration with every edge costing 1; same arguments, state,
+ * stats and errors. */
+kairos_status kairos_temporal_bfs(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, int32_t strict,
+                                  uint32_t *out, kairos_duration_stats *stats);
+
 /* ---- launch shape ----------------------------------------------------------------- */
 
 kairos_status kairos_get_tuning(const kairos_graph *g, kairos_tuning *t);

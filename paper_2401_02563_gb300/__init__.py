@@ -112,6 +112,8 @@ SIGNATURES = {
                                            ctypes.POINTER(kairos_fastest_stats)]),
     "kairos_shortest_duration": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
                                                 ctypes.c_int32, _P, ctypes.POINTER(kairos_duration_stats)]),
+    "kairos_temporal_bfs": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_int32, _P, ctypes.POINTER(kairos_duration_stats)]),
     "kairos_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
     "kairos_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
     "kairos_autotune": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32,
@@ -302,6 +304,15 @@ def kairos_shortest_duration(g, n, src, ta, tw, out, strict=0):
     return st
 
 
+def kairos_temporal_bfs(g, n, src, ta, tw, out, strict=0):
+    """Temporal BFS levels (least number of edges) from src into out; returns the stats."""
+    _check_out(out, n)
+    st = kairos_duration_stats()
+    _check(lib().kairos_temporal_bfs(g, int(src), int(ta), int(tw), int(strict), _ptr(out), ctypes.byref(st)),
+           "kairos_temporal_bfs")
+    return st
+
+
 def kairos_earliest_arrival_noalloc(g, n, src, ta, tw, out):
     """Earliest arrival that allocates no device memory; out must be a CUDA tensor."""
     _check_out(out, n)
@@ -452,6 +463,9 @@ class Graph:
 
     def shortest_duration(self, src, ta, tw, out, strict=0):
         return kairos_shortest_duration(self.handle, self.n, src, ta, tw, out, strict)
+
+    def temporal_bfs(self, src, ta, tw, out, strict=0):
+        return kairos_temporal_bfs(self.handle, self.n, src, ta, tw, out, strict)
 
     def batch(self, queries, out, want_stats=True):
         return kairos_batch_query(self.handle, self.n, queries, out, want_stats)

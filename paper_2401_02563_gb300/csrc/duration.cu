@@ -1,5 +1,6 @@
 // Shortest durations (least total travel time; the "shortest path" among the minimal temporal
-// paths of Sec. 2.3) as a label-correcting computation over edge labels.
+// paths of Sec. 2.3) and temporal BFS (least number of edges; Table 4's T. BFS read over
+// time-respecting paths) as one label-correcting computation over edge labels.
 //
 // For a usable edge e = (u, v, t, lam) let D(e) be the least total duration of a
 // time-respecting path from the source that ends with e, and let
@@ -137,7 +138,7 @@ __global__ void sd_relax_kernel(const SdChunk *__restrict__ chunks, const unsign
                                 const LamT *__restrict__ lam, const uint32_t *__restrict__ pred,
                                 const uint32_t *__restrict__ slot, uint32_t *d, const uint32_t *__restrict__ sm,
                                 uint8_t *changed, uint32_t *from_next, uint32_t *hislot, int32_t src, uint32_t ta,
-                                uint32_t tw, unsigned long long *ctr) {
+                                uint32_t tw, int unit, unsigned long long *ctr) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -158,7 +159,8 @@ __global__ void sd_relax_kernel(const SdChunk *__restrict__ chunks, const unsign
                 b = p != SD_NONE ? sm[p] : INF;
             }
             if (b == INF) continue;
-            const uint32_t cand = b + li;  // a path's total duration: at most tw - ta
+            // a path's total duration (at most tw - ta) or its number of edges (at most n - 1)
+            const uint32_t cand = b + (unit ? 1u : li);
             const uint32_t j = slot[i];
             if (cand < d[j]) {  // the label may be stale (never below the current one)
                 const int32_t v = dst[i];
@@ -353,8 +355,10 @@ void release_duration_scratch(kairos_graph *g) {
 
 using namespace kairos;
 
-extern "C" kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw,
-                                                  int32_t strict, uint32_t *out, kairos_duration_stats *stats) {
+// Least total cost from src: the durations (unit = 0, shortest durations) or one per edge
+// (unit = 1, temporal BFS).
+static kairos_status least_cost(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, int32_t strict, int unit,
+                                uint32_t *out, kairos_duration_stats *stats) {
     if (!g || !out) return fail(KAIROS_ERR_INVALID_ARG, "shortest duration: NULL argument");
     if (src < 0 || (int64_t)src >= g->n) return fail(KAIROS_ERR_INVALID_ARG, "shortest duration: source out of range");
     if (ta > tw || tw > TMAX) return fail(KAIROS_ERR_INVALID_ARG, "shortest duration: need ta <= tw <= KAIROS_TIME_MAX");
@@ -396,12 +400,12 @@ extern "C" kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, 
             sd_relax_kernel<uint16_t><<<rgrid, 256, 0, s>>>(chunks, chunk_count, g->fwd.dst, g->fwd.t,
                                                             (const uint16_t *)g->fwd.lam, pred, w.sd_slot, w.sd_d,
                                                             w.sd_sm, w.sd_changed, from_next, hislot, src, ta, tw,
-                                                            w.sd_ctr);
+                                                            unit, w.sd_ctr);
         else
             sd_relax_kernel<uint32_t><<<rgrid, 256, 0, s>>>(chunks, chunk_count, g->fwd.dst, g->fwd.t,
                                                             (const uint32_t *)g->fwd.lam, pred, w.sd_slot, w.sd_d,
                                                             w.sd_sm, w.sd_changed, from_next, hislot, src, ta, tw,
-                                                            w.sd_ctr);
+                                                            unit, w.sd_ctr);
         KAIROS_CUDA(cudaGetLastError(), "shortest duration: relax");
         KAIROS_CUDA(cudaMemcpyAsync(w.sd_ctr_host, w.sd_ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
                     "shortest duration: flag");
@@ -436,4 +440,14 @@ extern "C" kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, 
         stats->examined_edges = w.sd_ctr_host[1];
     }
     return KAIROS_OK;
+}
+
+extern "C" kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw,
+                                                  int32_t strict, uint32_t *out, kairos_duration_stats *stats) {
+    return least_cost(g, src, ta, tw, strict, 0, out, stats);
+}
+
+extern "C" kairos_status kairos_temporal_bfs(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, int32_t strict,
+                                             uint32_t *out, kairos_duration_stats *stats) {
+    return least_cost(g, src, ta, tw, strict, 1, out, stats);
 }

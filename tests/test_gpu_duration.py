@@ -136,3 +136,48 @@ def test_medium_workload_full_size():
         ta, tw = (0, (1 << 24) - 1) if i == 0 else (1 << 22, 3 << 22)
         assert np.array_equal(gpu_sd(g, el.n, s, ta, tw)[0], orc.shortest_duration(s, ta, tw, 0)), (s, ta, tw)
     g.close()
+
+
+# ---- temporal BFS: the same computation with unit costs --------------------------------
+
+def gpu_bfs(g, n, s, ta, tw, strict=0, on_device=True):
+    out = (torch.full((n,), 0x5A5A5A5A, dtype=torch.int32, device="cuda") if on_device
+           else np.full(n, 0x5A5A5A5A, np.uint32))
+    st = g.temporal_bfs(s, ta, tw, out, strict)
+    return labels(out), st
+
+
+def test_temporal_bfs_hand_example_and_random_graphs():
+    gj = json.load(open(os.path.join(HERE, "golden", "hand_example.json")))
+    el = Edges(gj["n"], gj["edges_u_v_t_lam"])
+    g = kx.Graph.from_edges(el)
+    for c in gj["temporal_bfs_cases"]:
+        for on_device in (True, False):
+            assert gpu_bfs(g, el.n, c["vertex"], c["ta"], c["tw"], c["strict"], on_device)[0].tolist() == c["expect"], c
+    g.close()
+    for seed in range(4):
+        n, m = 400 + 131 * seed, 8000 + 1000 * seed
+        el = synth.random_small(n, m, 0x7D00 + seed, t_max=50, lam_max=5, lam_min=0)
+        orc = Oracle(el)
+        g = kx.Graph.from_edges(el)
+        out_deg = np.bincount(el.src, minlength=n)
+        for k, s in enumerate(np.flatnonzero(out_deg)[[1, 7]]):
+            for strict in (0, 1):
+                ta, tw = (0, 10**6) if k == 0 else (5, 40)
+                want = orc.temporal_bfs(int(s), ta, tw, strict)
+                assert np.array_equal(gpu_bfs(g, n, int(s), ta, tw, strict, bool(strict))[0], want), (seed, s, strict)
+        g.close()
+
+
+def test_temporal_bfs_tiny_workload():
+    el = synth.rmat(synth.WORKLOADS[1].graph)
+    orc = Oracle(el)
+    g = kx.Graph.from_edges(el)
+    for i, s in enumerate(synth.pick_vertices(el, 4, 0x5D5F, True, False)):
+        ta, tw = (0, 2**20 - 1) if i % 2 == 0 else (1 << 18, 3 << 18)
+        want = orc.temporal_bfs(s, ta, tw, i % 2)
+        got, st = gpu_bfs(g, el.n, s, ta, tw, i % 2)
+        assert np.array_equal(got, want), (s, ta, tw)
+        # alternating with shortest durations on the same graph reuses the per-graph state
+        assert np.array_equal(gpu_sd(g, el.n, s, ta, tw, i % 2)[0], orc.shortest_duration(s, ta, tw, i % 2))
+    g.close()
