@@ -208,7 +208,8 @@ kairos_status kairos_fastest_path(kairos_graph *g, int32_t src, uint32_t ta, uin
  * Method: label-correcting rounds over edge labels D(e) = lambda_e + f_u(t_e), where f_u(tau)
  * is the least label of u's in-edges arriving by tau, kept as suffix minima over u's in-edges
  * in the reversed graph's order; at most n rounds.  The first call builds the reverse-slot
- * map of the edges (one radix sort) and three per-edge uint32 arrays, kept with the graph.
+ * map of the edges (one radix sort) and per-edge uint32 arrays (reverse slot, label, suffix
+ * minimum, and per predicate used the in-time slot), kept with the graph and freed with it.
  * Needs the reverse graph (not built with skip_reverse: INVALID_ARG).  out: uint32_t[n], host
  * or device.  stats (may be NULL): rounds and usable edges examined.  Synchronous.
  * Errors: INVALID_ARG, TIMEOUT (round cap), OOM, CUDA. */

@@ -9,8 +9,9 @@
 // Then D(e) = lam + f_u(t) and the answer at v != src is the minimum D over v's in-edges.
 // Every round relaxes the out-edges of the vertices whose f changed, and then recomputes
 // f for the heads whose in-edge labels dropped.  f_u is a suffix minimum over u's in-edges
-// in the reversed graph's order (latest arrival first), so one binary search over the
-// reversed list's mirrored times finds the in-edges that arrive in time.  Labels only fall,
+// in the reversed graph's order (latest arrival first); the slot from which the in-edges
+// arrive in time for an out-edge depends only on the graph, so it is found once per graph
+// (a binary search over the reversed list's mirrored times) and kept.  Labels only fall,
 // and after k rounds every path of k edges is accounted for; simple paths suffice, so at
 // most n rounds.
 // Work per round follows the changes: when an in-edge label of u drops, f_u changes only from
