@@ -393,3 +393,54 @@ def test_concurrent_launches(tiny, lanes):
         assert [s.relaxed_edges for s in stats] == counts
         torch.cuda.synchronize()
         g.close()
+
+
+class BudgetAllocator(kx.TorchAllocator):
+    """Device allocations through PyTorch, refused (NULL) once `budget` bytes would be live:
+    device out-of-memory injected on the host."""
+
+    def __init__(self, budget):
+        super().__init__()
+        self.budget = budget
+        self.live = {}
+
+    def _alloc(self, nbytes, ctx):
+        if sum(self.live.values()) + int(nbytes) > self.budget:
+            return None
+        p = super()._alloc(nbytes, ctx)
+        if p:
+            self.live[int(p)] = int(nbytes)
+        return p
+
+    def _free(self, ptr, ctx):
+        if ptr:
+            self.live.pop(int(ptr), None)
+        super()._free(ptr, ctx)
+
+
+def test_allocator_refusals_return_oom(tiny):
+    """A refused allocation at graph build or at query time returns KAIROS_ERR_OOM, gives
+    back what was taken, and leaves the graph usable once memory is available again."""
+    el, orc, _ = tiny
+    A = BudgetAllocator(0)
+    with pytest.raises(kx.KairosError) as e:
+        kx.Graph.from_edges(el, allocator=A)
+    assert e.value.status == kx.KAIROS_ERR_OOM
+    assert not A.live
+    A.budget = 1 << 62
+    g = kx.Graph.from_edges(el, allocator=A)
+    A.budget = sum(A.live.values()) + 4096  # the graph fits, a 32-lane workspace does not
+    g.set_tuning(lanes=32)
+    qs = tiny_queries(el, 32)
+    out = torch.empty((len(qs), el.n), dtype=torch.int32, device="cuda")
+    with pytest.raises(kx.KairosError) as e:
+        g.batch(qs, out, want_stats=False)
+    assert e.value.status == kx.KAIROS_ERR_OOM
+    A.budget = 1 << 62
+    g.batch(qs, out, want_stats=False)
+    got = labels(out)
+    for i, q in enumerate(qs):
+        assert np.array_equal(got[i], orc.query(q)), q
+    g.close()
+    torch.cuda.synchronize()
+    assert not A.live  # closing the graph gave back every allocation
