@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "trace.h"
 
 using namespace kairos;
 
@@ -429,6 +430,7 @@ kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs
 extern "C" {
 
 kairos_status kairos_graph_build(const kairos_edge_list *el, const kairos_graph_opts *opts, kairos_graph **out) {
+    TraceRange tr("kairos_graph_build");
     if (!el || !out) return fail(KAIROS_ERR_INVALID_ARG, "graph build: NULL argument");
     const int64_t n = el->n_vertices, m = el->n_edges;
     if (n < 1 || n >= (1LL << 31)) return fail(KAIROS_ERR_INVALID_ARG, "graph build: need 1 <= n_vertices < 2^31");
@@ -518,6 +520,7 @@ kairos_status kairos_graph_build(const kairos_edge_list *el, const kairos_graph_
 }
 
 kairos_status kairos_index_build(kairos_graph *g, uint32_t threshold) {
+    TraceRange tr("kairos_index_build");
     if (!g) return fail(KAIROS_ERR_INVALID_ARG, "index build: NULL graph");
     std::lock_guard<std::mutex> lk(g->mu);
     if (threshold == 0) threshold = 1;
@@ -584,6 +587,7 @@ kairos_status kairos_batch_query(kairos_graph *g, const kairos_query *qs, int32_
         if (st != KAIROS_OK) return st;
     }
     std::lock_guard<std::mutex> lk(g->mu);
+    TraceRange tr("kairos_batch_query");
     return kairos_run_queries(g, qs, n, out, stats, g->tuning.lanes);
 }
 
@@ -598,6 +602,7 @@ static kairos_status single(kairos_graph *g, int kind, int32_t v, uint32_t ta, u
     kairos_status st = check_query(g, q);
     if (st != KAIROS_OK) return st;
     std::lock_guard<std::mutex> lk(g->mu);
+    TraceRange tr(kind == KAIROS_EA ? "kairos_earliest_arrival" : "kairos_latest_departure");
     return kairos_run_queries(g, &q, 1, out, nullptr, 1);
 }
 

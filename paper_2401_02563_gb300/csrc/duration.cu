@@ -25,6 +25,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "trace.h"
 
 namespace kairos {
 namespace {
@@ -367,6 +368,7 @@ static kairos_status least_cost(kairos_graph *g, int32_t src, uint32_t ta, uint3
     if (!g->has_rev)
         return fail(KAIROS_ERR_INVALID_ARG, "shortest duration: the graph was built without its reverse (skip_reverse)");
     std::lock_guard<std::mutex> lk(g->mu);
+    TraceRange tr(unit ? "kairos_temporal_bfs" : "kairos_shortest_duration");
     kairos_status st = ensure_duration_state(g);
     if (st == KAIROS_OK) st = ensure_pred(g, strict);
     if (st != KAIROS_OK) return st;

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "trace.h"
 
 namespace kairos {
 namespace {
@@ -133,6 +134,7 @@ extern "C" kairos_status kairos_fastest_path(kairos_graph *g, int32_t src, uint3
     if (ta > tw || tw > TMAX) return fail(KAIROS_ERR_INVALID_ARG, "fastest path: need ta <= tw <= KAIROS_TIME_MAX");
     if (strict != 0 && strict != 1) return fail(KAIROS_ERR_INVALID_ARG, "fastest path: strict is 0 or 1");
     std::lock_guard<std::mutex> lk(g->mu);
+    TraceRange tr("kairos_fastest_path");
     cudaStream_t s = g->stream;
     const int64_t n = g->n;
     kairos_fastest_stats fs;

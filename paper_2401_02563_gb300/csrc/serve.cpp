@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "trace.h"
 
 using clk = std::chrono::steady_clock;
 using namespace kairos;
@@ -222,6 +223,7 @@ void admit(kairos_server *V, Session &S, int q, uint64_t id) {
 // `share` sessions launch together, each with 1/share of the resident blocks when the graph's
 // tuning keeps two launches in flight.
 kairos_status launch_session(kairos_server *V, Session &S, int share) {
+    TraceRange tr(S.kind == KAIROS_EA ? "serve slice (earliest arrival)" : "serve slice (latest departure)");
     kairos_graph *g = V->g;
     cudaStream_t s = S.s;
     EdgeMapArgs a = session_args(g, S);
