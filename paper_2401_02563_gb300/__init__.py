@@ -133,6 +133,72 @@ SIGNATURES = {
 }
 
 
+def graph_fingerprint(n_vertices, src, dst, t_dep, lam, samples=4096) -> str:
+    """A short hash of a graph's size and of evenly spaced samples of its edge arrays (host
+    arrays or torch tensors): equal graphs agree; different ones almost surely differ."""
+    import hashlib
+    h = hashlib.sha256()
+    m = int(src.shape[0])
+    h.update(f"{int(n_vertices)}:{m}".encode())
+    if m == 0:
+        return h.hexdigest()[:24]
+    idx = np.unique(np.linspace(0, m - 1, num=min(samples, m)).astype(np.int64))
+    try:
+        for a in (src, dst, t_dep, lam):
+            if isinstance(a, np.ndarray):
+                part = np.ascontiguousarray(a[idx])
+            else:  # a torch tensor: gather through a signed view (unsigned types index poorly)
+                import torch
+                v = a.view(torch.int16) if a.element_size() == 2 else a.view(torch.int32)
+                part = v[torch.as_tensor(idx, device=a.device)].cpu().numpy()
+            h.update(f"{part.dtype.itemsize}".encode())
+            h.update(part.tobytes())
+    except Exception:  # the fingerprint only keys the autotune cache: never fail a build over it
+        h.update(b"unsampled")
+    return h.hexdigest()[:24]
+
+
+_lib_digest = None
+
+
+def _library_digest() -> str:
+    global _lib_digest
+    if _lib_digest is None:
+        import hashlib
+        with open(library_path(), "rb") as fh:
+            _lib_digest = hashlib.sha256(fh.read()).hexdigest()[:16]
+    return _lib_digest
+
+
+def _device_name() -> str:
+    import torch
+    return torch.cuda.get_device_name()
+
+
+def autotune_cache_key(graph, sample) -> str:
+    import hashlib
+    qarr, k = make_queries(sample)
+    qh = hashlib.sha256(ctypes.string_at(ctypes.addressof(qarr), ctypes.sizeof(kairos_query) * k)).hexdigest()[:16]
+    return "|".join([graph.fingerprint, str(graph.theta), qh, _device_name(), _library_digest()])
+
+
+def _read_cache(path) -> dict:
+    import json
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (FileNotFoundError, ValueError):
+        return {}
+
+
+def _write_cache(path, table) -> None:
+    import json
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as fh:
+        json.dump(table, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class KairosError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: status {status}: {message}")
@@ -441,6 +507,8 @@ class Graph:
     def __init__(self, n_vertices, src, dst, t_dep, lam, stream=None, allocator=None, skip_reverse=False):
         self.n = int(n_vertices)
         self.m = int(src.shape[0])
+        self.theta = KAIROS_NO_INDEX
+        self.fingerprint = graph_fingerprint(n_vertices, src, dst, t_dep, lam)
         self._allocator = allocator  # keeps the callbacks alive as long as the graph
         self.handle = kairos_graph_build(n_vertices, src, dst, t_dep, lam, stream, allocator, skip_reverse)
 
@@ -450,6 +518,7 @@ class Graph:
 
     def index(self, threshold):
         kairos_index_build(self.handle, threshold)
+        self.theta = int(threshold)
         return self
 
     def earliest_arrival(self, src, ta, tw, out):
@@ -476,8 +545,21 @@ class Graph:
     def set_tuning(self, **fields):
         return kairos_set_tuning(self.handle, **fields)
 
-    def autotune(self, sample):
-        return kairos_autotune(self.handle, sample)
+    def autotune(self, sample, cache=None):
+        """Time launch shapes on `sample` and install the fastest.  With `cache` (a JSON file
+        path), a shape already found for this graph, index threshold, query sample, GPU model and
+        library build is installed without measuring, and a new one is stored."""
+        if cache is None:
+            return kairos_autotune(self.handle, sample)
+        key = autotune_cache_key(self, sample)
+        table = _read_cache(cache)
+        if key in table:
+            return kairos_set_tuning(self.handle, **table[key])
+        best = kairos_autotune(self.handle, sample)
+        table = _read_cache(cache)  # re-read: another process may have added entries
+        table[key] = {name: int(getattr(best, name)) for name, _ in kairos_tuning._fields_}
+        _write_cache(cache, table)
+        return best
 
     def autotune_index(self, sample, thetas=(16, 64, 256, 1024, 4096, KAIROS_NO_INDEX)):
         return kairos_autotune_index(self.handle, sample, thetas)
