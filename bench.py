@@ -6,8 +6,10 @@ edge-map on the device-resident graph (64 earliest-arrival + 64 latest-departure
 full window, on the 2^20-vertex, 2^25-edge bursty R-MAT graph with the selective index at
 degree 256).  The graph build (ingest, sort, index) is timed separately.
 
-Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead, on a
-bounded sample of the same workload.
+Prints one JSON line (rank 0).  Beside the timed steps it reports the same queries one per
+launch, end to end through host memory, served through the continuous-batching server, and
+the other path queries on the same graph (fastest paths, shortest durations, temporal BFS).
+`--impl reference` times the CPU oracle instead, on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
