@@ -80,6 +80,21 @@ def test_null_arguments_are_rejected_without_a_device(library):
     assert library.kairos_graph_build(None, None, ctypes.byref(h)) == kx.KAIROS_ERR_INVALID_ARG
     assert library.kairos_index_build(None, 16) == kx.KAIROS_ERR_INVALID_ARG
     assert library.kairos_earliest_arrival(None, 0, 0, 1, None) == kx.KAIROS_ERR_INVALID_ARG
+    for fn in (library.kairos_fastest_path, library.kairos_shortest_duration, library.kairos_temporal_bfs):
+        assert fn(None, 0, 0, 1, 0, None, None) == kx.KAIROS_ERR_INVALID_ARG
     assert b"NULL" in library.kairos_last_error()
     library.kairos_graph_free(None)
     library.kairos_serve_destroy(None)
+
+
+def test_readme_c_example_compiles_and_links(tmp_path, library):
+    """The C example of the README builds against the header and links against the library
+    (running it needs a GPU)."""
+    import re
+    text = open(os.path.join(ROOT, "README.md")).read()
+    code = re.search(r"```c\n(.*?)```", text, re.S).group(1)
+    src = tmp_path / "example.c"
+    src.write_text(code)
+    libdir = os.path.dirname(kx.library_path())
+    subprocess.check_call(["gcc", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                           str(tmp_path / "example"), "-L", libdir, "-lkairos", f"-Wl,-rpath,{libdir}"])
