@@ -50,7 +50,8 @@ def build(force: bool = False) -> str:
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".{os.getpid()}.tmp"
-            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-fno-semantic-interposition", "-shared", "-pthread",
+                                   "-ffp-contract=off",
                                    "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB

@@ -118,10 +118,20 @@ static double normal(uint64_t seed, uint64_t i, uint32_t d0, uint32_t dmax) {
  * with H(x) = ((x)^(1-s) - 1)/(1-s) the integral of x^-s.  Returns rank - 1. */
 static double zipf_h(double x, double s) { return (det_exp((1.0 - s) * det_log(x)) - 1.0) / (1.0 - s); }
 static double zipf_hinv(double y, double s) { return det_exp(det_log(1.0 + y * (1.0 - s)) / (1.0 - s)); }
-static uint64_t zipf(uint64_t seed, uint64_t i, uint32_t d0, uint32_t dmax, uint64_t n, double s) {
-    double hx0 = zipf_h(1.5, s) - 1.0; /* H(3/2) - h(1) */
-    double hn = zipf_h((double)n + 0.5, s);
-    double ss = 2.0 - zipf_hinv(zipf_h(2.5, s) - det_exp(-s * det_log(2.0)), s);
+/* The constants of one (N, s): H(3/2) - h(1), H(N + 1/2) and the squeeze bound. */
+typedef struct {
+    double hx0, hn, ss;
+} zipf_consts;
+static zipf_consts zipf_setup(uint64_t n, double s) {
+    zipf_consts z;
+    z.hx0 = zipf_h(1.5, s) - 1.0;
+    z.hn = zipf_h((double)n + 0.5, s);
+    z.ss = 2.0 - zipf_hinv(zipf_h(2.5, s) - det_exp(-s * det_log(2.0)), s);
+    return z;
+}
+static uint64_t zipf(const zipf_consts *zc, uint64_t seed, uint64_t i, uint32_t d0, uint32_t dmax, uint64_t n,
+                     double s) {
+    const double hx0 = zc->hx0, hn = zc->hn, ss = zc->ss;
     for (uint32_t d = d0; d < dmax; ++d) {
         double u = hn + u01(synth_draw(seed, i, d)) * (hx0 - hn);
         double x = zipf_hinv(u, s);
@@ -164,20 +174,17 @@ static void *run(void *arg) {
     const synth_params *p = J->p;
     const double ab = p->a + p->b, abc = p->a + p->b + p->c;
     const uint64_t sd = p->seed;
+    const zipf_consts zc = zipf_setup(p->t_span, p->zipf_s); /* used by the Zipf model only */
     for (int64_t i = J->lo; i < J->hi; ++i) {
         uint64_t u = 0, v = 0;
         for (int l = 0; l < p->scale; ++l) {
+            /* quadrant of level l: [0, a) none, [a, a+b) v, [a+b, a+b+c) u, else both
+             * (selected without branches: the draws are independent across levels) */
             double r = u01(synth_draw(sd, (uint64_t)i, (uint32_t)l));
-            uint64_t bit = 1ULL << (p->scale - 1 - l);
-            if (r < p->a) {
-            } else if (r < ab) {
-                v |= bit;
-            } else if (r < abc) {
-                u |= bit;
-            } else {
-                u |= bit;
-                v |= bit;
-            }
+            const uint64_t ge_a = r >= p->a, ge_ab = r >= ab, ge_abc = r >= abc;
+            const int sh = p->scale - 1 - l;
+            u |= ge_ab << sh;
+            v |= ((ge_a & (ge_ab ^ 1u)) | ge_abc) << sh;
         }
         J->src[i] = (int32_t)scramble(u, p->scale, sd);
         J->dst[i] = (int32_t)scramble(v, p->scale, sd);
@@ -197,7 +204,7 @@ static void *run(void *arg) {
                 tt = below(synth_draw(sd, (uint64_t)i, D_TIME + 1), p->t_span);
             }
         } else {
-            tt = zipf(sd, (uint64_t)i, D_TIME, D_TIME_END, p->t_span, p->zipf_s);
+            tt = zipf(&zc, sd, (uint64_t)i, D_TIME, D_TIME_END, p->t_span, p->zipf_s);
         }
         J->t[i] = (uint32_t)tt;
 
@@ -259,4 +266,7 @@ int synth_rmat(const synth_params *p, int32_t *src, int32_t *dst, uint32_t *t, v
 /* Exposed for tests of the deterministic elementary functions. */
 double synth_det_log(double x) { return det_log(x); }
 double synth_det_exp(double x) { return det_exp(x); }
-uint64_t synth_zipf_rank(uint64_t seed, uint64_t i, uint64_t n, double s) { return zipf(seed, i, 0, 128, n, s); }
+uint64_t synth_zipf_rank(uint64_t seed, uint64_t i, uint64_t n, double s) {
+    const zipf_consts zc = zipf_setup(n, s);
+    return zipf(&zc, seed, i, 0, 128, n, s);
+}
