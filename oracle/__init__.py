@@ -72,6 +72,9 @@ def _load():
                                         ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _P,
                                         ctypes.POINTER(ctypes.c_int64)]
         L.oracle_certify_ea.restype = ctypes.c_int
+        L.oracle_certify_ea_rows.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_int,
+                                             _P, _P, _P, _P, _P, _P, _P]
+        L.oracle_certify_ea_rows.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -85,7 +88,7 @@ def _arrays(el):
 
 
 class Oracle:
-    """The oracle bound to one edge list: sorts it by departure time once (qsort), then
+    """The oracle bound to one edge list: sorts it by departure time once (stable radix sort), then
     answers queries by the one-pass scans of oracle.c."""
 
     def __init__(self, el):
@@ -183,6 +186,107 @@ def mirror_edges(src, dst, t, lam):
     equals C minus earliest arrival on the mirror in [C - tw, C - ta]."""
     t2 = (np.uint64(C_MIRROR) - (t.astype(np.uint64) + lam.astype(np.uint64))).astype(np.uint32)
     return dst.copy(), src.copy(), t2, lam.astype(np.uint32)
+
+
+class Certifier:
+    """The any-size certificate (`certify_ea` above) for many queries of both kinds on one
+    edge list, with the arrays converted once.  Latest-departure labels are certified
+    through the mirror identity of `mirror_edges`: LD[u] = C - EA'[u], where EA' is
+    earliest arrival from the target on the reversed graph with departures C - (t + lam)
+    over the window [C - tw, C - ta] (same predicate).  The mirrored graph reuses the
+    source and head arrays (swapped) and adds only its departure times, computed in chunks.
+    `check_all` runs the single-threaded C checks of independent queries on a thread pool
+    (the C calls release the interpreter lock)."""
+
+    def __init__(self, el):
+        self.n = int(el.n)
+        self.src, self.dst, self.t, self.lam = _arrays(el)
+        self.m = int(self.src.shape[0])
+        self._t_mirror = None
+        self._mu = threading.Lock()
+
+    def _mirror_times(self):
+        with self._mu:
+            if self._t_mirror is None:
+                t2 = np.empty(self.m, np.uint32)
+                step = 1 << 24
+                for a in range(0, self.m, step):
+                    b = min(self.m, a + step)
+                    t2[a:b] = (np.uint64(C_MIRROR) - (self.t[a:b].astype(np.uint64) +
+                                                      self.lam[a:b].astype(np.uint64))).astype(np.uint32)
+                self._t_mirror = t2
+        return self._t_mirror
+
+    def check(self, q, labels):
+        """(status, bad) of one query's labels: 0 holds, 1 fails, 2 not applicable."""
+        labels = np.ascontiguousarray(labels, np.uint32)
+        bad = ctypes.c_int64(0)
+        if q.kind == 0:
+            src, dst, t, ta, tw, lab = self.src, self.dst, self.t, q.ta, q.tw, labels
+        else:
+            src, dst, t = self.dst, self.src, self._mirror_times()
+            ta, tw = C_MIRROR - q.tw, C_MIRROR - q.ta
+            lab = np.where(labels == UNREACHED, np.uint32(UNREACHED),
+                           (np.uint32(C_MIRROR) - labels).astype(np.uint32))
+        rc = _load().oracle_certify_ea(self.n, self.m, src.ctypes.data, dst.ctypes.data, t.ctypes.data,
+                                       self.lam.ctypes.data, int(q.vertex), int(ta), int(tw), int(q.strict),
+                                       lab.ctypes.data, ctypes.byref(bad))
+        if rc < 0:
+            raise ValueError("oracle_certify_ea: invalid arguments")
+        return rc, int(bad.value)
+
+    def check_group(self, queries, labels):
+        """Certify up to 32 queries of one kind in one pass over the edges (the rows form of
+        the certificate); labels[i] (a sequence, or a callable of i) is query i's label
+        array, fetched one at a time.  Returns [(status, bad)]."""
+        w = len(queries)
+        assert 1 <= w <= 32 and len({q.kind for q in queries}) == 1
+        ld = queries[0].kind == 1
+        rows = np.empty((self.n, w), np.uint32)  # vertex-major: the w labels of a vertex together
+        for i in range(w):
+            lab = np.asarray(labels(i) if callable(labels) else labels[i], np.uint32)
+            rows[:, i] = (np.where(lab == UNREACHED, np.uint32(UNREACHED),
+                                   (np.uint32(C_MIRROR) - lab).astype(np.uint32)) if ld else lab)
+        s = np.array([q.vertex for q in queries], np.int32)
+        ta = np.array([C_MIRROR - q.tw if ld else q.ta for q in queries], np.uint32)
+        tw = np.array([C_MIRROR - q.ta if ld else q.tw for q in queries], np.uint32)
+        st = np.array([q.strict for q in queries], np.int32)
+        status = np.zeros(w, np.int32)
+        bad = np.zeros(w, np.int64)
+        src, dst, t = (self.dst, self.src, self._mirror_times()) if ld else (self.src, self.dst, self.t)
+        rc = _load().oracle_certify_ea_rows(self.n, self.m, src.ctypes.data, dst.ctypes.data, t.ctypes.data,
+                                            self.lam.ctypes.data, w, s.ctypes.data, ta.ctypes.data,
+                                            tw.ctypes.data, st.ctypes.data, rows.ctypes.data,
+                                            status.ctypes.data, bad.ctypes.data)
+        if rc < 0:
+            raise ValueError("oracle_certify_ea_rows: invalid arguments")
+        return [(int(a), int(b)) for a, b in zip(status, bad)]
+
+    def check_all(self, queries, rows, threads=None, group=None):
+        """Certify query i against rows(i) (a callable returning that query's labels as a
+        host array) for every i: queries of one kind are certified `group` at a time in one
+        edge pass (default: enough groups to occupy `threads`, at most 16 queries each),
+        `threads` groups at once.  Returns the list of (status, bad) in order."""
+        from concurrent.futures import ThreadPoolExecutor
+        if any(q.kind == 1 for q in queries):
+            self._mirror_times()
+        cores = threads or os.cpu_count() or 1
+        if group is None:
+            group = max(1, min(16, -(-len(queries) // cores)))
+        groups = []
+        for kind in (0, 1):
+            idx = [i for i, q in enumerate(queries) if q.kind == kind]
+            groups += [idx[c:c + group] for c in range(0, len(idx), group)]
+        threads = min(len(groups), cores) or 1
+        out = [None] * len(queries)
+
+        def run(gi):
+            for i, r in zip(gi, self.check_group([queries[i] for i in gi], lambda k: rows(gi[k]))):
+                out[i] = r
+
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(run, groups))
+        return out
 
 
 # ---- brute force over simple paths (pure Python, tiny graphs only) ---------------------
@@ -321,7 +425,6 @@ def brute_shortest_duration(n, src, dst, t, lam, s, ta, tw, strict=0):
 def brute_temporal_bfs(n, src, dst, t, lam, s, ta, tw, strict=0):
     """Least number of edges over vertex-simple time-respecting paths from s (a cycle cut out of
     a time-respecting walk leaves a shorter time-respecting walk)."""
-    ones = np.ones(len(src), np.uint32)
     out = [UNREACHED] * n
     out[s] = 0
     adj = [[] for _ in range(n)]
@@ -344,6 +447,5 @@ def brute_temporal_bfs(n, src, dst, t, lam, s, ta, tw, strict=0):
             go(v, te + le, hops + 1, False, onpath)
             onpath.discard(v)
 
-    del ones
     go(s, ta, 0, True, {s})
     return np.array(out, np.uint32)

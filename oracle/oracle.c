@@ -38,28 +38,64 @@
  * (credited in Sec. 7): edges are visited in ascending t (descending for latest
  * departure), and every edge sharing the same t is re-swept until nothing changes, which
  * only matters when a zero-duration edge under Succeeds can enable another edge of the
- * same instant.  The sort is the C library's qsort.
+ * same instant.  The time order is a plain stable radix sort of the edge indices.
  */
 #include <stdint.h>
 #include <stdlib.h>
 
 #define UNREACHED 0xFFFFFFFFu
 
-static int cmp_u64(const void *a, const void *b) {
-    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
-    return (x > y) - (x < y);
-}
-
-/* perm[k] = index of the k-th edge in ascending departure time (ties by edge index).
- * Requires m < 2^32.  Returns 0, or -1 on bad arguments / allocation failure. */
+/* perm[k] = index of the k-th edge in ascending departure time, ties by edge index (the
+ * stable order).  A least-significant-digit radix sort of (t, index) pairs: three stable
+ * counting passes over 11-bit digits of t, starting from ascending indices, so equal
+ * times keep ascending indices.  Requires m < 2^32.  Returns 0, or -1 on bad arguments /
+ * allocation failure. */
 int oracle_time_order(int64_t m, const uint32_t *t, uint32_t *perm) {
     if (m < 0 || m > (int64_t)0xFFFFFFFFLL || (m > 0 && (!t || !perm))) return -1;
-    uint64_t *key = (uint64_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(uint64_t));
-    if (!key) return -1;
-    for (int64_t i = 0; i < m; ++i) key[i] = ((uint64_t)t[i] << 32) | (uint64_t)i;
-    qsort(key, (size_t)m, sizeof(uint64_t), cmp_u64);
-    for (int64_t i = 0; i < m; ++i) perm[i] = (uint32_t)(key[i] & 0xFFFFFFFFu);
+    if (m == 0) return 0;
+    uint32_t *idx2 = (uint32_t *)malloc((size_t)m * sizeof(uint32_t));
+    uint32_t *key = (uint32_t *)malloc((size_t)m * sizeof(uint32_t));
+    uint32_t *key2 = (uint32_t *)malloc((size_t)m * sizeof(uint32_t));
+    int64_t *count = (int64_t *)malloc(2048 * sizeof(int64_t));
+    if (!idx2 || !key || !key2 || !count) {
+        free(idx2);
+        free(key);
+        free(key2);
+        free(count);
+        return -1;
+    }
+    for (int64_t i = 0; i < m; ++i) {
+        perm[i] = (uint32_t)i;
+        key[i] = t[i];
+    }
+    uint32_t *ki = key, *ko = key2, *ii = perm, *io = idx2;
+    for (int shift = 0; shift < 33; shift += 11) { /* digits 0-10, 11-21, 22-31 */
+        for (int d = 0; d < 2048; ++d) count[d] = 0;
+        for (int64_t i = 0; i < m; ++i) ++count[(ki[i] >> shift) & 2047u];
+        int64_t run = 0; /* exclusive prefix sums: first slot of each digit */
+        for (int d = 0; d < 2048; ++d) {
+            int64_t c = count[d];
+            count[d] = run;
+            run += c;
+        }
+        for (int64_t i = 0; i < m; ++i) {
+            int64_t slot = count[(ki[i] >> shift) & 2047u]++;
+            ko[slot] = ki[i];
+            io[slot] = ii[i];
+        }
+        uint32_t *x = ki;
+        ki = ko;
+        ko = x;
+        x = ii;
+        ii = io;
+        io = x;
+    }
+    /* after three passes the indices sit in idx2 */
+    for (int64_t i = 0; i < m; ++i) perm[i] = ii[i];
+    free(idx2);
     free(key);
+    free(key2);
+    free(count);
     return 0;
 }
 
@@ -229,6 +265,76 @@ int oracle_certify_ea(int64_t n, int64_t m, const int32_t *src, const int32_t *d
             *bad = v;
             return 1;
         }
+    free(seen);
+    return 0;
+}
+
+/*
+ * The same certificate for w <= 32 earliest-arrival labellings at once, in one pass over
+ * the edges: query q has source s[q], window [ta[q], tw[q]], predicate strict[q] and labels
+ * ea[v * w + q] (vertex-major rows, so that the w labels of one vertex are read together).
+ * Each query gets the three checks of oracle_certify_ea, independently of the others:
+ * status[q] = 0 holds, 1 fails (bad[q] as in oracle_certify_ea), 2 not applicable.
+ * Returns 0, or -1 on bad arguments or allocation failure.
+ */
+int oracle_certify_ea_rows(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                           const uint32_t *lam, int w, const int32_t *s, const uint32_t *ta, const uint32_t *tw,
+                           const int32_t *strict, const uint32_t *ea, int32_t *status, int64_t *bad) {
+    if (n <= 0 || m < 0 || w < 1 || w > 32 || !s || !ta || !tw || !strict || !ea || !status || !bad) return -1;
+    int any_zero = 0;
+    for (int64_t e = 0; e < m && !any_zero; ++e) any_zero = lam[e] == 0;
+    uint32_t live = 0; /* queries still unrefuted */
+    for (int q = 0; q < w; ++q) {
+        if (s[q] < 0 || s[q] >= n || ta[q] > tw[q]) return -1;
+        status[q] = 0;
+        bad[q] = 0;
+        if (any_zero && !strict[q]) {
+            status[q] = 2;
+            continue;
+        }
+        if (ea[(int64_t)s[q] * w + q] != ta[q]) {
+            status[q] = 1;
+            bad[q] = s[q];
+            continue;
+        }
+        live |= 1u << q;
+    }
+    for (int64_t v = 0; v < n; ++v)
+        for (int q = 0; q < w; ++q) {
+            uint32_t x = ea[v * w + q];
+            if (((live >> q) & 1u) && v != s[q] && x != UNREACHED && !(x > ta[q] && x <= tw[q])) {
+                status[q] = 1;
+                bad[q] = v;
+                live &= ~(1u << q);
+            }
+        }
+    uint32_t *seen = (uint32_t *)calloc((size_t)n, sizeof(uint32_t)); /* bit q: v witnessed in query q */
+    if (!seen) return -1;
+    for (int64_t e = 0; e < m; ++e) {
+        const uint32_t *au_row = ea + (int64_t)src[e] * w, *av_row = ea + (int64_t)dst[e] * w;
+        for (int q = 0; q < w; ++q) {
+            if (!((live >> q) & 1u)) continue;
+            uint32_t au = au_row[q];
+            if (au == UNREACHED) continue;
+            if ((strict[q] && src[e] != s[q]) ? !(au < t[e]) : !(au <= t[e])) continue;
+            uint64_t arrive = (uint64_t)t[e] + lam[e];
+            if (arrive > tw[q]) continue;
+            if ((uint64_t)av_row[q] > arrive) { /* closure violated */
+                status[q] = 1;
+                bad[q] = -(e + 1);
+                live &= ~(1u << q);
+                continue;
+            }
+            if ((uint64_t)av_row[q] == arrive) seen[dst[e]] |= 1u << q;
+        }
+    }
+    for (int64_t v = 0; v < n; ++v)
+        for (int q = 0; q < w; ++q)
+            if (((live >> q) & 1u) && v != s[q] && ea[v * w + q] != UNREACHED && !((seen[v] >> q) & 1u)) {
+                status[q] = 1; /* no witness */
+                bad[q] = v;
+                live &= ~(1u << q);
+            }
     free(seen);
     return 0;
 }

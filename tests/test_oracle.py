@@ -219,6 +219,55 @@ def test_certificate_rejects_planted_mistakes(tiny_workload):
     assert certify_ea(el, s, 0, tw, 0, x)[0] == 1
 
 
+def test_time_order_is_the_stable_sort():
+    """The oracle's radix time order equals a library stable sort by departure time (ties by
+    edge index), on times with many ties and on the extremes of the 32-bit range."""
+    lib = oracle._load()
+    rng = np.random.default_rng(0x50127)
+    cases = [np.zeros(0, np.uint32), np.array([7], np.uint32),
+             np.array([0xFFFFFFFF, 0, 0xFFFFFFFF, 1, 0, 0x80000000, 2047, 2048, 1 << 22], np.uint32),
+             rng.integers(0, 5, 10_000).astype(np.uint32),
+             rng.integers(0, 1 << 32, 100_000, dtype=np.uint64).astype(np.uint32),
+             (rng.zipf(1.2, 100_000) % (1 << 31)).astype(np.uint32)]
+    for t in cases:
+        perm = np.empty(t.size, np.uint32)
+        assert lib.oracle_time_order(t.size, t.ctypes.data, perm.ctypes.data) == 0
+        assert np.array_equal(perm, np.argsort(t, kind="stable").astype(np.uint32))
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_certifier_both_kinds(tiny_workload, strict):
+    """The batch certifier accepts the oracle's earliest-arrival and latest-departure labels
+    (latest departure through the mirrored graph) and rejects single-label mistakes in
+    either kind."""
+    el, orc = tiny_workload
+    cert = oracle.Certifier(el)
+    vs = synth.pick_vertices(el, 3, 0x7800 + strict, True, True)
+    qs = [Query(k, v, ta, tw, strict) for v in vs for k in (EA, LD)
+          for ta, tw in ((0, C_MIRROR), (1000, 900_000))]
+    labs = [orc.query(q) for q in qs]
+    assert cert.check_all(qs, lambda i: labs[i], threads=4) == [(0, 0)] * len(qs)
+    assert cert.check_all(qs, lambda i: labs[i], threads=2, group=3) == [(0, 0)] * len(qs)
+    for i, q in enumerate(qs[:4]):
+        lab = labs[i]
+        reached = np.flatnonzero((lab != UNREACHED) & (np.arange(el.n) != q.vertex))
+        unreached = np.flatnonzero(lab == UNREACHED)
+        assert reached.size > 10 and unreached.size > 0
+        v = int(reached[reached.size // 3])
+        for bad in (lab[v] + 1, lab[v] - 1, UNREACHED):
+            x = lab.copy()
+            x[v] = bad
+            assert cert.check(q, x)[0] == 1, (q, bad)
+            # the rows form refutes the same mistake and only in that query of its group
+            same = [j for j in range(len(qs)) if qs[j].kind == q.kind]
+            res = cert.check_group([qs[j] for j in same], [x if j == i else labs[j] for j in same])
+            assert [r[0] for r in res] == [1 if j == i else 0 for j in same], (q, bad)
+        x = lab.copy()
+        x[int(unreached[0])] = q.tw if q.kind == EA else q.ta
+        assert cert.check(q, x)[0] == 1, q
+        assert cert.check_group([q], [x])[0][0] == 1, q
+
+
 def test_invalid_arguments_rejected():
     el = from_rows(3, [(0, 1, 1, 1)])
     orc = Oracle(el)
