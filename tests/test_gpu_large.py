@@ -1,7 +1,9 @@
-"""Full-size parity for the large workloads (2^28 and 2^31 edges).  Labels are checked by
-the any-size certificate (closed under every usable edge, every finite label witnessed,
-exact when durations are >= 1), one query against the oracle's full scan at 2^28 edges,
-and latest departure against the oracle on a smaller graph of the same laws."""
+"""Full-size parity for the large workloads (2^28 and 2^31 edges).  Every answer of both
+kinds is checked by the any-size certificate (closed under every usable edge, every finite
+label witnessed; exact when durations are >= 1, which holds on these graphs): earliest
+arrival directly, latest departure through the mirrored graph.  One query per window
+extreme is also compared with the oracle's full scan at 2^28 edges, and the 2^31-edge
+workload's laws are compared label by label on a smaller graph."""
 import numpy as np
 import pytest
 
@@ -26,42 +28,54 @@ def labels(t):
     return t.cpu().numpy().view(np.uint32)
 
 
+def certify_all(cert, qs, out):
+    """Certificate of every row of the device tensor `out` (row i answers qs[i])."""
+    res = cert.check_all(qs, lambda i: labels(out[i]))
+    bad = [(qs[i], r) for i, r in enumerate(res) if r != (0, 0)]
+    assert not bad, bad[:4]
+
+
 @pytest.fixture(scope="module")
 def batched_graph():
     w = synth.WORKLOADS[3]
     el = synth.rmat(w.graph)
     g = kx.Graph.from_edges(el, stream=torch.cuda.Stream())
-    g.index(256)
-    yield el, g
+    g.index(16)
+    yield el, g, oracle.Certifier(el)
     g.close()
 
 
 def test_batched_workload_full_size(batched_graph):
-    el, g = batched_graph
-    qs = synth.workload_queries(3, el)[:32]
-    g.set_tuning(lanes=16)
+    """Workload 3: all 256 random-window queries in the autotuned launch shape, every answer
+    certified; the shortest and the longest window also against the oracle's scan."""
+    el, g, cert = batched_graph
+    qs = synth.workload_queries(3, el)
+    assert len(qs) == 256
+    g.autotune(qs[:64])
     out = torch.empty((len(qs), el.n), dtype=torch.int32, device="cuda")
     stats = g.batch(qs, out)
     torch.cuda.synchronize()
-    got = labels(out)
-    for i in range(0, len(qs), 4):
-        q = qs[i]
-        assert oracle.certify_ea(el, q.vertex, q.ta, q.tw, q.strict, got[i]) == (0, 0), q
-        assert got[i][q.vertex] == q.ta
-        assert stats[i].reached == int((got[i] != UNREACHED).sum())
+    certify_all(cert, qs, out)
+    for i, q in enumerate(qs):
+        assert stats[i].reached == int((out[i] != -1).sum().item()), q
+    lens = [q.tw - q.ta for q in qs]
     orc = Oracle(el)
-    want = orc.query(qs[1])
-    assert np.array_equal(got[1], want)
-    assert stats[1].relaxed_edges == orc.admissible(qs[1], want)
+    for i in (int(np.argmin(lens)), int(np.argmax(lens))):
+        want = orc.query(qs[i])
+        assert np.array_equal(labels(out[i]), want), qs[i]
+        assert stats[i].relaxed_edges == orc.admissible(qs[i], want)
+    g.set_tuning(lanes=1, concurrent=1)
 
 
 def test_served_workload_full_size_alone_and_in_the_mix(batched_graph):
     """Workload 4: the resident workload-3 graph, a 70/30 mix with log-uniform windows
-    submitted while others run; each answer equals the same query alone."""
-    el, g = batched_graph
+    submitted while others run; each answer equals the same query alone, and every answer is
+    certified."""
+    el, g, cert = batched_graph
     qs = synth.workload_queries(4, el, count=48)
+    assert {q.kind for q in qs} == {EA, LD}
     alone = torch.empty((len(qs), el.n), dtype=torch.int32, device="cuda")
-    g.set_tuning(lanes=1)
+    g.set_tuning(lanes=1, concurrent=1)
     g.batch(qs, alone, want_stats=False)
     server = kx.kairos_serve_create(g.handle, max_slots=16, rounds_per_slice=3)
     outs = [torch.empty(el.n, dtype=torch.int32, device="cuda") for _ in qs]
@@ -71,33 +85,56 @@ def test_served_workload_full_size_alone_and_in_the_mix(batched_graph):
     finally:
         kx.kairos_serve_destroy(server)
     torch.cuda.synchronize()
-    ref = labels(alone)
     for i, q in enumerate(qs):
         assert infos[i].status == kx.KAIROS_OK
-        got = labels(outs[i])
-        assert np.array_equal(got, ref[i]), q
-        if q.kind == EA and i % 6 == 0:
-            assert oracle.certify_ea(el, q.vertex, q.ta, q.tw, q.strict, got) == (0, 0), q
+        assert torch.equal(outs[i], alone[i]), q
+        assert infos[i].reached == int((outs[i] != -1).sum().item()), q
+    certify_all(cert, qs, torch.stack(outs))
 
 
-def test_large_skewed_full_size():
-    """Workload 5: 2^26 vertices, 2^31 edges, Zipf(1.2) times, 16-bit durations."""
+@pytest.fixture(scope="module")
+def large_skewed():
     w = synth.WORKLOADS[5]
     el = synth.rmat(w.graph)
     assert el.lam.dtype == np.uint16 and el.m == 1 << 31
-    g = kx.Graph.from_edges(el, stream=torch.cuda.Stream(), skip_reverse=True)
-    g.index(256)
-    qs = [q for q in synth.workload_queries(5, el, count=2) if q.kind == EA]
-    g.set_tuning(lanes=2)
-    out = torch.empty((len(qs), el.n), dtype=torch.int32, device="cuda")
-    stats = g.batch(qs, out)
-    torch.cuda.synchronize()
-    got = labels(out)
+    g = kx.Graph.from_edges(el, stream=torch.cuda.Stream())
+    yield el, g
     g.close()
+
+
+def test_large_skewed_full_size(large_skewed):
+    """Workload 5 (2^26 vertices, 2^31 edges, Zipf(1.2) times, 16-bit durations): the 64-way
+    batch of earliest-arrival and latest-departure queries, full window.  The answers at
+    index threshold 16 and 32 lanes are certified one by one; 16 lanes, threshold 4096 and
+    the one-query-per-launch path must give the same labels and the same relaxed-edge counts."""
+    el, g = large_skewed
+    qs = synth.workload_queries(5, el)
+    assert len(qs) == 128 and {q.kind for q in qs} == {EA, LD}
+    ref = torch.empty((len(qs), el.n), dtype=torch.int32, device="cuda")
+    g.index(16)
+    g.set_tuning(lanes=32, concurrent=2, warp_max_edges=128, chunk_edges=512, dense_div=16, relax_mode=0)
+    ref_stats = g.batch(qs, ref)
+    torch.cuda.synchronize()
     for i, q in enumerate(qs):
-        assert got[i][q.vertex] == q.ta
-        assert stats[i].relaxed_edges > 0
-        assert oracle.certify_ea(el, q.vertex, q.ta, q.tw, q.strict, got[i]) == (0, 0), q
+        assert labels(ref[i][q.vertex:q.vertex + 1])[0] == (q.ta if q.kind == EA else q.tw)
+        assert ref_stats[i].relaxed_edges > 0
+    certify_all(oracle.Certifier(el), qs, ref)
+    out = torch.empty_like(ref)
+    for theta, lanes in ((16, 16), (4096, 32), (4096, 16)):
+        g.index(theta)
+        g.set_tuning(lanes=lanes)
+        out.fill_(0x5A5A5A5A)
+        st = g.batch(qs, out)
+        torch.cuda.synchronize()
+        for i, q in enumerate(qs):
+            assert torch.equal(out[i], ref[i]), (theta, lanes, q)
+            assert st[i].relaxed_edges == ref_stats[i].relaxed_edges, (theta, lanes, q)
+    g.set_tuning(lanes=1, concurrent=1)
+    row = torch.empty(el.n, dtype=torch.int32, device="cuda")
+    for i in (0, 64):
+        q = qs[i]
+        (g.earliest_arrival if q.kind == EA else g.latest_departure)(q.vertex, q.ta, q.tw, row)
+        assert torch.equal(row, ref[i]), q
 
 
 @pytest.mark.parametrize("theta", [16, 4096])
