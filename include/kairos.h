@@ -306,9 +306,14 @@ void kairos_serve_destroy(kairos_server *s);
  * The first call on a device looks the array up (cudaGetSymbolAddress); make that first
  * call before any stream capture.  Every call on a device shares the array: calls whose
  * GPU work can overlap (other streams, other threads without ordering) race on it and
- * must be serialised by the caller.  Synchronous on the graph's stream.
- * Errors: INVALID_ARG (NULL, host out, vertex or window out of range, graph over the
- * limits), TIMEOUT, CUDA. */
+ * must be serialised by the caller.  Synchronous on the graph's stream: it enqueues
+ * memsets, a launch and small reads there and waits for them.  A caller that runs it
+ * while another thread captures a CUDA graph must have built the graph with its own
+ * stream (kairos_graph_opts.stream, not the legacy default stream, whose work would
+ * invalidate a capture elsewhere), and that stream must not be the one being captured.
+ * Errors: INVALID_ARG (NULL, out not device memory of the current device, vertex or
+ * window out of range, graph over the limits), TIMEOUT (a device wait or the round cap
+ * ran out), CUDA. */
 kairos_status kairos_earliest_arrival_noalloc(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, uint32_t *out);
 
 /* ---- diagnostics -------------------------------------------------------------------- */

@@ -536,6 +536,11 @@ class Graph:
     def temporal_bfs(self, src, ta, tw, out, strict=0):
         return kairos_temporal_bfs(self.handle, self.n, src, ta, tw, out, strict)
 
+    def earliest_arrival_noalloc(self, src, ta, tw, out):
+        """kairos_earliest_arrival_noalloc: earliest arrival into the device buffer `out`
+        (n labels) with no device allocation."""
+        return kairos_earliest_arrival_noalloc(self.handle, self.n, src, ta, tw, out)
+
     def batch(self, queries, out, want_stats=True):
         return kairos_batch_query(self.handle, self.n, queries, out, want_stats)
 

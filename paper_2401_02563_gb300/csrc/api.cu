@@ -33,6 +33,11 @@ kairos_status cuda_fail(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? KAIROS_ERR_OOM : KAIROS_ERR_CUDA;
 }
 
+void apply_test_hooks(EdgeMapArgs &a) {
+    if (const char *v = getenv("KAIROS_SPIN_LIMIT")) a.spin_limit = strtoull(v, nullptr, 10);
+    if (const char *v = getenv("KAIROS_ROUND_CAP")) a.max_rounds = (uint32_t)strtoul(v, nullptr, 10);
+}
+
 void *Allocator::get(size_t bytes) const {
     if (bytes == 0) bytes = 1;
     if (alloc) return alloc(bytes, ctx);
@@ -211,10 +216,7 @@ EdgeMapArgs make_args(kairos_graph *g, const Csr &c, const LaneParams &lp, uint3
     a.lanes = lp;
     a.max_rounds = (uint32_t)std::min<int64_t>(n + 1, 0xFFFFFFF0LL);
     a.spin_limit = DEFAULT_SPIN_LIMIT;
-    // test hooks: shrink the device wait limit or the round cap to exercise the TIMEOUT
-    // paths without a fault or a hang (read per call)
-    if (const char *v = getenv("KAIROS_SPIN_LIMIT")) a.spin_limit = strtoull(v, nullptr, 10);
-    if (const char *v = getenv("KAIROS_ROUND_CAP")) a.max_rounds = (uint32_t)strtoul(v, nullptr, 10);
+    apply_test_hooks(a);
     a.warp_max_edges = g->tuning.warp_max_edges;
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;

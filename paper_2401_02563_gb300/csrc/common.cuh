@@ -167,6 +167,11 @@ cudaError_t retire_lanes(uint32_t *arr, uint32_t *prev, int64_t n, int W, const 
 // Seed lane q at source src with label ta into the frontier of round r (bitmap + queue).
 cudaError_t seed_lane(const EdgeMapArgs &a, int W, int q, int32_t src, uint32_t ta, uint32_t r, cudaStream_t s);
 
+// Test hooks read from the environment on every call: KAIROS_SPIN_LIMIT (polls of every
+// bounded device wait) and KAIROS_ROUND_CAP (edge-map rounds) shrink the limits so that the
+// TIMEOUT paths can be exercised without a fault or a hang.
+void apply_test_hooks(EdgeMapArgs &a);
+
 // Launch one persistent edge-map (cooperative: every block resident).
 cudaError_t edgemap_launch(const EdgeMapArgs &a, int lanes, int lam_bits, int grid, cudaStream_t s);
 // Largest co-resident grid for this lane width (blocks per SM * SMs), 0 on error.

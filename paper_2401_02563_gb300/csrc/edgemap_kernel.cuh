@@ -958,12 +958,15 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 || W == 16) ? 4 : (W == 32
 template <int W, int MODE, typename LamT>
 cudaError_t launch_t(const EdgeMapArgs &a, int grid, cudaStream_t s) {
     const size_t smem = sizeof(WarpSmem<W>) * (EM_THREADS / 32);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(edgemap_kernel<W, MODE, LamT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    // the shared-memory attribute is per device: set it once on each device that launches
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        e = cudaFuncSetAttribute(edgemap_kernel<W, MODE, LamT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        if (dev >= 0 && dev < 64) configured[dev] = true;
     }
     void *args[] = {(void *)&a};
     return cudaLaunchCooperativeKernel((void *)edgemap_kernel<W, MODE, LamT>, dim3(grid), dim3(EM_THREADS), args, smem, s);

@@ -93,11 +93,15 @@ extern "C" kairos_status kairos_earliest_arrival_noalloc(kairos_graph *g, int32_
     if (g->n > NA_MAX_VERTICES)
         return fail(KAIROS_ERR_INVALID_ARG,
                     "no-allocation query: the graph has more than 2^20 vertices, the limit of the fixed scratch array");
+    int dev = 0;
+    KAIROS_CUDA(cudaGetDevice(&dev), "no-allocation query: current device");
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, out) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
         cudaGetLastError();
         return fail(KAIROS_ERR_INVALID_ARG, "no-allocation query: out must be device memory");
     }
+    if (at.device != dev)
+        return fail(KAIROS_ERR_INVALID_ARG, "no-allocation query: out must be memory of the current device");
     std::lock_guard<std::mutex> lk(g->mu);
     unsigned char *base = nullptr;
     kairos_status st = scratch_address(&base);
@@ -158,6 +162,7 @@ extern "C" kairos_status kairos_earliest_arrival_noalloc(kairos_graph *g, int32_
     a.round_end = 0xFFFFFFFFu;
     a.running_mask = 0xFFFFFFFFu;
     a.spin_limit = DEFAULT_SPIN_LIMIT;
+    apply_test_hooks(a);
     int bps = 0;
     int grid = edgemap_max_grid(1, g->lam_bits, 0, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "no-allocation query: no resident launch shape");
