@@ -1,7 +1,7 @@
 """ORACLE -- test infrastructure only.
 
 Plain CPU statement of the temporal path queries (earliest arrival, latest departure,
-fastest path, shortest duration, temporal BFS),
+fastest path, shortest duration, temporal BFS) and of temporal connected components,
 used by the test suite, the package smoke check and the CPU-baseline leg of the
 benchmark, and by nothing in the library.  `oracle.c` holds the single-threaded one-pass
 scans; this module loads it and adds pure-Python brute force over simple paths for tiny
@@ -75,6 +75,9 @@ def _load():
         L.oracle_certify_ea_rows.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_int,
                                              _P, _P, _P, _P, _P, _P, _P]
         L.oracle_certify_ea_rows.restype = ctypes.c_int
+        L.oracle_temporal_cc.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_uint32,
+                                         ctypes.c_uint32, _P]
+        L.oracle_temporal_cc.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -164,6 +167,43 @@ class Oracle:
         return int(L.oracle_admissible_ld(self.m, self.dst.ctypes.data, self.t.ctypes.data,
                                           self.lam.ctypes.data, labels.ctypes.data, int(q.vertex),
                                           int(q.ta), int(q.strict)))
+
+
+def temporal_cc(el, ta: int, tw: int) -> np.ndarray:
+    """Temporal connected components in [ta, tw] (see oracle.c): the smallest vertex id of each
+    vertex's component in the undirected graph of the window's usable edges."""
+    src, dst, t, lam = _arrays(el)
+    out = np.empty(int(el.n), np.uint32)
+    rc = _load().oracle_temporal_cc(int(el.n), int(src.shape[0]), src.ctypes.data, dst.ctypes.data, t.ctypes.data,
+                                    lam.ctypes.data, int(ta), int(tw), out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_temporal_cc: invalid arguments or allocation failure")
+    return out
+
+
+def brute_temporal_cc(n, src, dst, t, lam, ta, tw):
+    """Components by breadth-first search over the window's usable edges (tiny graphs)."""
+    adj = [[] for _ in range(n)]
+    for u, v, x, y in zip(src, dst, t, lam):
+        if _usable(int(x), int(y), ta, tw):
+            adj[int(u)].append(int(v))
+            adj[int(v)].append(int(u))
+    out = [None] * n
+    for s in range(n):
+        if out[s] is not None:
+            continue
+        comp, stack = [s], [s]
+        out[s] = -1
+        while stack:
+            x = stack.pop()
+            for y in adj[x]:
+                if out[y] is None:
+                    out[y] = -1
+                    comp.append(y)
+                    stack.append(y)
+        for x in comp:
+            out[x] = min(comp)
+    return np.array(out, np.uint32)
 
 
 def certify_ea(el, s: int, ta: int, tw: int, strict: int, labels: np.ndarray):

@@ -582,3 +582,37 @@ int oracle_temporal_bfs(int64_t n, int64_t m, const int32_t *src, const int32_t 
                         uint32_t *out) {
     return least_cost_scan(n, m, src, dst, t, lam, perm, s, ta, tw, strict, 1, out);
 }
+
+/*
+ * Temporal connected components within [ta, tw] (the connectivity application of Sec. 2.3 and
+ * Table 4, "adapted to accept a start and end time" as Sec. 6 describes): the connected
+ * components of the undirected graph formed by the edges usable in the window (t >= ta and
+ * t + lam <= tw), every vertex included.  out[v] = the smallest vertex id of v's component (a
+ * vertex with no usable edge is its own component).  A plain union-find: every usable edge
+ * unites its endpoints (the root is the smaller id, found by following parents with path
+ * halving); then each vertex takes its root.  Returns 0, or -1 on bad arguments / allocation.
+ */
+static int32_t uf_find(int32_t *parent, int32_t x) {
+    while (parent[x] != x) {
+        parent[x] = parent[parent[x]];
+        x = parent[x];
+    }
+    return x;
+}
+
+int oracle_temporal_cc(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const uint32_t *t,
+                       const uint32_t *lam, uint32_t ta, uint32_t tw, uint32_t *out) {
+    if (n <= 0 || m < 0 || ta > tw || !out || (m > 0 && (!src || !dst || !t || !lam))) return -1;
+    int32_t *parent = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!parent) return -1;
+    for (int64_t v = 0; v < n; ++v) parent[v] = (int32_t)v;
+    for (int64_t e = 0; e < m; ++e) {
+        if (t[e] < ta || (uint64_t)t[e] + lam[e] > tw) continue; /* not usable in the window */
+        int32_t a = uf_find(parent, src[e]), b = uf_find(parent, dst[e]);
+        if (a == b) continue;
+        if (a < b) parent[b] = a; else parent[a] = b; /* the smaller id stays the root */
+    }
+    for (int64_t v = 0; v < n; ++v) out[v] = (uint32_t)uf_find(parent, (int32_t)v);
+    free(parent);
+    return 0;
+}

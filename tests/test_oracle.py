@@ -460,3 +460,42 @@ def test_temporal_bfs_reductions_and_invariants(tiny_workload, strict):
         reached = orc.earliest_arrival(s, ta, tw, strict) != UNREACHED
         assert np.array_equal(hops != UNREACHED, reached)
         assert np.all(hops[reached] <= sd[reached])
+
+
+# ---- temporal connected components --------------------------------------------------------
+
+def _canonical(labels):
+    """Relabel a component labelling by the smallest vertex of each component."""
+    labels = np.asarray(labels)
+    first = {}
+    for v, c in enumerate(labels.tolist()):
+        first.setdefault(c, v)
+    return np.array([first[c] for c in labels.tolist()], np.uint32)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_temporal_cc_brute_force(seed):
+    """Union-find over the window's usable edges equals breadth-first search on tiny graphs
+    (self-loops, parallel edges, zero durations, windows cutting edges at both ends)."""
+    n = 5 + seed % 13
+    el = synth.random_small(n, 3 + 2 * seed, 0x7C00 + seed, t_max=30, lam_max=6, lam_min=0)
+    for ta, tw in ((0, 40), (5, 20), (12, 12), (0, C_MIRROR)):
+        got = oracle.temporal_cc(el, ta, tw)
+        want = oracle.brute_temporal_cc(n, el.src, el.dst, el.t, el.lam, ta, tw)
+        assert got.tolist() == want.tolist(), (seed, ta, tw)
+
+
+def test_temporal_cc_equals_scipy_components():
+    """A library routine on the same snapshot: scipy's connected components of the window's
+    usable edges, relabelled by each component's smallest vertex."""
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    import scipy.sparse as sp
+
+    el = synth.rmat(synth.WORKLOADS[1].graph)
+    for ta, tw in ((0, (1 << 20) - 1), (100_000, 300_000), (500_000, 500_300)):
+        use = (el.t >= ta) & (el.t.astype(np.uint64) + el.lam <= tw)
+        a = sp.coo_matrix((np.ones(int(use.sum())), (el.src[use], el.dst[use])), shape=(el.n, el.n))
+        _, lab = csgraph.connected_components(a, directed=True, connection="weak")
+        got = oracle.temporal_cc(el, ta, tw)
+        assert got.tolist() == _canonical(lab).tolist()
+        assert all(got[v] <= v for v in range(el.n))
