@@ -108,7 +108,8 @@ typedef struct {
 
 /* Launch-shape knobs of the edge-map; kairos_autotune picks them per graph. */
 typedef struct {
-    int32_t lanes;          /* queries relaxed together per launch: 1, 2, 4, 8, 16 or 32 */
+    int32_t lanes;          /* queries relaxed together per launch: 1, 2, 4, 8, 16, 32, or 64
+                               (64 with relax_mode 3 only) */
     int32_t blocks_per_sm;  /* resident 256-thread blocks per SM of the persistent grid; 0: as many as fit */
     int32_t warp_max_edges; /* a vertex's range longer than this is split across the grid */
     int32_t chunk_edges;    /* edges per grid-wide chunk of a split range (multiple of 32) */
@@ -120,12 +121,26 @@ typedef struct {
                                check, fetching only segments with candidate lanes, pass by pass
                                (suits few active lanes); 1: lower it with a fire-and-forget
                                atomic for every usable edge and take the next frontier from the
-                               bitmap of touched heads */
+                               bitmap of touched heads; 3 (lanes 32 or 64): sweep all edges once in
+                               departure-time order, block by block, relaxing every lane whose
+                               label at the tail allows the departure, and finish chains inside a
+                               block with frontier rounds restricted to that block (the first
+                               call builds a time-ordered copy of the edges, 16 bytes per edge
+                               and direction, kept with the graph); calls with fewer lanes (single
+                               queries) run mode 0 */
     int32_t concurrent;     /* launches of one call kept in flight together, each on its own stream
                                and workspace with 1/concurrent of the resident blocks (unless
                                blocks_per_sm is set): 1 or 2 (0 means 1).  2 lets one launch's
                                sparse final rounds overlap another's busy ones; it applies when the
                                outputs are device memory and the call has two or more launches */
+    int32_t block_edges;    /* relax_mode 3: edges per time block (an instant is never split);
+                               0: max(4096, n_edges / 512) */
+    int32_t select_permille; /* selective access (Sec. 5.1, Eq. 3) for the frontier modes 0-2:
+                               with histograms built (kairos_selectivity_build), an indexed vertex
+                               whose estimated selectivity for the departure interval being
+                               expanded exceeds select_permille / 1000 has its whole list scanned
+                               instead of searched; 0: the index threshold alone decides.  Results
+                               never depend on it */
 } kairos_tuning;
 
 typedef struct {
@@ -156,6 +171,31 @@ kairos_status kairos_graph_build(const kairos_edge_list *edges, const kairos_gra
  * KAIROS_NO_INDEX drops the index (every list scanned).  Results never depend on it.
  * Errors: INVALID_ARG (NULL graph), OOM, CUDA. */
 kairos_status kairos_index_build(kairos_graph *g, uint32_t threshold);
+
+/* Selectivity histograms (Sec. 5.2): for every vertex with degree >= min_degree, in both
+ * directions, a 2D density histogram of its edges over start time and duration, each cut into
+ * 100 equal buckets over the vertex's own span (bucket i of starts holds the edges with
+ * (t - tmin) * 100 / (tmax - tmin + 1) == i; likewise durations).  A temporal predicate
+ * "departure in [a, b], arrival by tw" is estimated by counting every edge of a bucket whose
+ * centre satisfies it (the centre of a bucket is the floor of the mean of its first and last
+ * integer).  The edge-map uses the estimate for the access choice of tuning.select_permille.
+ * KAIROS_NO_INDEX drops the histograms.  Memory: about 40 KB per such vertex and direction.
+ * Errors: INVALID_ARG (NULL graph), OOM, CUDA. */
+kairos_status kairos_selectivity_build(kairos_graph *g, uint32_t min_degree);
+
+/* For each of the n vertices (host array) of the forward lists (kind KAIROS_EA) or of the
+ * reversed, time-mirrored lists (KAIROS_LD): estimate[i] = the histogram's estimate of the edges
+ * departing in [a, b] and arriving by tw (UINT64_MAX for a vertex without a histogram), and, when
+ * exact is not NULL, exact[i] = the true number of such edges.  Host outputs.  Synchronous.
+ * Errors: INVALID_ARG (NULL, vertex out of range, LD without the reverse graph), OOM, CUDA. */
+kairos_status kairos_selectivity_estimate(kairos_graph *g, int32_t kind, const int32_t *vertices, int32_t n,
+                                          uint32_t a, uint32_t b, uint32_t tw, uint64_t *estimate, uint64_t *exact);
+
+/* The stored histogram of one vertex: meta4 = {tmin, start span S, lmin, duration span D} and
+ * counts[i * 100 + j] = edges in start bucket i and duration bucket j (host arrays).  Errors:
+ * INVALID_ARG (NULL, no histogram for the vertex), OOM, CUDA. */
+kairos_status kairos_selectivity_histogram(kairos_graph *g, int32_t kind, int32_t vertex, uint64_t *meta4,
+                                           uint32_t *counts);
 
 void kairos_graph_free(kairos_graph *g); /* NULL is ignored; waits for the graph's stream */
 
@@ -229,6 +269,18 @@ kairos_status kairos_shortest_duration(kairos_graph *g, int32_t src, uint32_t ta
 kairos_status kairos_temporal_bfs(kairos_graph *g, int32_t src, uint32_t ta, uint32_t tw, int32_t strict,
                                   uint32_t *out, kairos_duration_stats *stats);
 
+/* Temporal connected components within [ta, tw] (the temporal connectivity application of
+ * Sec. 2.3 and Table 4, adapted to a start and end time as Sec. 6 describes; the paper gives no
+ * further definition, and this reading is the components of the window's snapshot): the
+ * connected components of the undirected graph formed by the edges usable in the window
+ * (t >= ta and t + lambda <= tw), every vertex included.  out[v] = the smallest vertex id of
+ * v's component (v itself when it has no usable edge); out: uint32_t[n], host or device.
+ * Method: one pass of concurrent union-find over the usable edges (larger root linked under
+ * the smaller by compare-and-swap, path halving), then every vertex takes its root.
+ * Synchronous.  Errors: INVALID_ARG (NULL, ta > tw, tw > KAIROS_TIME_MAX), OOM, CUDA,
+ * INTERNAL (a link retry loop ran past its bound). */
+kairos_status kairos_temporal_cc(kairos_graph *g, uint32_t ta, uint32_t tw, uint32_t *out);
+
 /* ---- launch shape ----------------------------------------------------------------- */
 
 kairos_status kairos_get_tuning(const kairos_graph *g, kairos_tuning *t);
@@ -289,6 +341,36 @@ kairos_status kairos_serve_poll(kairos_server *s, uint64_t ticket, int64_t timeo
 /* Finish in-flight work, stop the thread and release the server.  NULL is ignored. */
 void kairos_serve_destroy(kairos_server *s);
 
+/* ---- one query stream over several server replicas --------------------------------------- */
+
+/* Queries are independent, so serving on several GPUs means one graph replica and one server
+ * per GPU (each built and created with that GPU current) behind one submission point; the
+ * replicas share nothing and nothing is exchanged between them (Sec. 8(e) of the plan: replicas,
+ * no collective).  A submission whose out buffer is device memory goes to the least-loaded
+ * replica on that buffer's device (its labels are written in place there); a host buffer goes
+ * to the least-loaded replica of all.  Load is submitted minus completed queries; ties go to the
+ * replica after the last one chosen; a replica whose queue is full passes the query on.  The
+ * router borrows the servers, which must outlive it.  Thread-safe. */
+typedef struct kairos_router kairos_router;
+
+/* servers: n >= 1 server handles.  Errors: INVALID_ARG (NULL, n < 1), OOM. */
+kairos_status kairos_router_create(kairos_server *const *servers, int32_t n, kairos_router **out);
+
+/* As kairos_serve_submit, on the replica chosen as above; *ticket is the router's.  Errors:
+ * INVALID_ARG (NULL, no replica on the device of a device buffer, or the replica's own checks),
+ * BUSY (every eligible replica's queue is full). */
+kairos_status kairos_router_submit(kairos_router *r, const kairos_query *q, uint32_t *out, uint64_t *ticket);
+
+/* As kairos_serve_poll on the replica that took the ticket (waits without blocking other
+ * callers).  Errors: INVALID_ARG (unknown ticket), NOT_READY. */
+kairos_status kairos_router_poll(kairos_router *r, uint64_t ticket, int64_t timeout_us, kairos_result_info *info);
+
+/* Per replica (in creation order, up to n): queries submitted to it and completed there (any
+ * array may be NULL).  Returns the number of replicas, 0 on a NULL router. */
+int32_t kairos_router_replica_counts(const kairos_router *r, uint64_t *submitted, uint64_t *completed, int32_t n);
+
+void kairos_router_destroy(kairos_router *r); /* NULL is ignored; the servers stay */
+
 /* ---- query without device allocation ------------------------------------------------------ */
 
 /* Earliest arrival from src within [ta, tw] under Succeeds, like kairos_earliest_arrival,
@@ -337,6 +419,13 @@ int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uin
  * barrier, other.  Zero unless the process ran with KAIROS_PHASE_CLOCK=1 in its
  * environment.  Returns 8, or 0 on a NULL argument.  Diagnostic only. */
 int32_t kairos_last_phase_cycles(const kairos_graph *g, uint64_t *cycles8);
+
+/* Counters of the last time-ordered (relax_mode 3) launch on g: out10 = {time blocks swept,
+ * fix-up rounds, fix-up vertices, edges read by fix-ups, records whose lanes were examined,
+ * records and edges read in all, then SM cycles summed over warps in block passes, fix-ups,
+ * grid barriers and initialisation plus read-out (the cycles are zero unless the process ran
+ * with KAIROS_PHASE_CLOCK=1)}.  Returns 10, or 0 on a NULL argument.  Diagnostic only. */
+int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out10);
 
 #ifdef __cplusplus
 }

@@ -69,7 +69,8 @@ class kairos_query_stats(ctypes.Structure):
 class kairos_tuning(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("warp_max_edges", ctypes.c_int32),
                 ("chunk_edges", ctypes.c_int32), ("dense_div", ctypes.c_int32), ("relax_mode", ctypes.c_int32),
-                ("concurrent", ctypes.c_int32)]
+                ("concurrent", ctypes.c_int32), ("block_edges", ctypes.c_int32),
+                ("select_permille", ctypes.c_int32)]
 
 
 class kairos_graph_info(ctypes.Structure):
@@ -130,6 +131,17 @@ SIGNATURES = {
     "kairos_last_round_profile": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P]),
     "kairos_last_phase_cycles": (ctypes.c_int32, [_P, _P]),
     "kairos_earliest_arrival_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, _P]),
+    "kairos_last_stream_profile": (ctypes.c_int32, [_P, _P]),
+    "kairos_temporal_cc": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, _P]),
+    "kairos_selectivity_build": (ctypes.c_int, [_P, ctypes.c_uint32]),
+    "kairos_selectivity_estimate": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_uint32,
+                                                   ctypes.c_uint32, ctypes.c_uint32, _P, _P]),
+    "kairos_selectivity_histogram": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "kairos_router_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "kairos_router_submit": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "kairos_router_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(kairos_result_info)]),
+    "kairos_router_replica_counts": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
+    "kairos_router_destroy": (None, [_P]),
 }
 
 
@@ -472,6 +484,72 @@ def kairos_serve_destroy(s):
     lib().kairos_serve_destroy(s)
 
 
+def kairos_temporal_cc(g, n, ta, tw, out):
+    """Component labels (smallest vertex id) of the window's snapshot into out (n labels)."""
+    _check_out(out, n)
+    _check(lib().kairos_temporal_cc(g, int(ta), int(tw), _ptr(out)), "kairos_temporal_cc")
+    return out
+
+
+def kairos_selectivity_build(g, min_degree):
+    _check(lib().kairos_selectivity_build(g, int(min_degree)), "kairos_selectivity_build")
+
+
+def kairos_selectivity_estimate(g, kind, vertices, a, b, tw, want_exact=True):
+    """(estimates, exact counts) for the vertices' lists (kind 0 forward, 1 reversed)."""
+    v = np.ascontiguousarray(vertices, np.int32)
+    est = np.zeros(v.size, np.uint64)
+    ex = np.zeros(v.size, np.uint64) if want_exact else None
+    _check(lib().kairos_selectivity_estimate(g, int(kind), v.ctypes.data, v.size, int(a), int(b), int(tw),
+                                             est.ctypes.data, ex.ctypes.data if want_exact else None),
+           "kairos_selectivity_estimate")
+    return est, ex
+
+
+def kairos_selectivity_histogram(g, kind, vertex):
+    """(tmin, S, lmin, D), counts[100][100] of one vertex's histogram."""
+    meta = np.zeros(4, np.uint64)
+    counts = np.zeros(100 * 100, np.uint32)
+    _check(lib().kairos_selectivity_histogram(g, int(kind), int(vertex), meta.ctypes.data, counts.ctypes.data),
+           "kairos_selectivity_histogram")
+    return tuple(int(x) for x in meta), counts.reshape(100, 100)
+
+
+def kairos_router_create(servers):
+    """One submission point over several servers (graph replicas, normally one per GPU)."""
+    arr = (_P * len(servers))(*servers)
+    r = _P()
+    _check(lib().kairos_router_create(arr, len(servers), ctypes.byref(r)), "kairos_router_create")
+    return r
+
+
+def kairos_router_submit(r, query, out) -> int:
+    q, _ = make_queries([query])
+    t = ctypes.c_uint64(0)
+    _check(lib().kairos_router_submit(r, q, _ptr(out), ctypes.byref(t)), "kairos_router_submit")
+    return t.value
+
+
+def kairos_router_poll(r, ticket, timeout_us=-1):
+    info = kairos_result_info()
+    st = lib().kairos_router_poll(r, int(ticket), int(timeout_us), ctypes.byref(info))
+    if st == KAIROS_ERR_NOT_READY:
+        return None
+    _check(st, "kairos_router_poll")
+    return info
+
+
+def kairos_router_replica_counts(r, n):
+    sub = np.zeros(n, np.uint64)
+    done = np.zeros(n, np.uint64)
+    k = lib().kairos_router_replica_counts(r, sub.ctypes.data, done.ctypes.data, n)
+    return sub[:k].tolist(), done[:k].tolist()
+
+
+def kairos_router_destroy(r):
+    lib().kairos_router_destroy(r)
+
+
 def kairos_last_error() -> str:
     return lib().kairos_last_error().decode()
 
@@ -490,6 +568,17 @@ def kairos_last_phase_cycles(g):
     c = np.zeros(8, np.uint64)
     lib().kairos_last_phase_cycles(g, c.ctypes.data)
     return dict(zip(PHASES, c.tolist()))
+
+
+STREAM_COUNTERS = ("blocks", "fix_rounds", "fix_vertices", "fix_edges", "candidates", "scanned",
+                   "pass_cycles", "fixup_cycles", "barrier_cycles", "init_readout_cycles")
+
+
+def kairos_last_stream_profile(g):
+    """Counters of the last time-ordered (relax_mode 3) launch (cycles need KAIROS_PHASE_CLOCK=1)."""
+    c = np.zeros(10, np.uint64)
+    lib().kairos_last_stream_profile(g, c.ctypes.data)
+    return dict(zip(STREAM_COUNTERS, c.tolist()))
 
 
 def kairos_last_round_profile(g, max_rounds=256):
@@ -535,6 +624,9 @@ class Graph:
 
     def temporal_bfs(self, src, ta, tw, out, strict=0):
         return kairos_temporal_bfs(self.handle, self.n, src, ta, tw, out, strict)
+
+    def temporal_cc(self, ta, tw, out):
+        return kairos_temporal_cc(self.handle, self.n, ta, tw, out)
 
     def earliest_arrival_noalloc(self, src, ta, tw, out):
         """kairos_earliest_arrival_noalloc: earliest arrival into the device buffer `out`

@@ -68,6 +68,21 @@ bool device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Where the kernels may write an output buffer directly: device memory as it is, and
+// page-locked host memory through its device mapping (the writes cross the CPU-GPU link
+// inside the launch, no staging copy).  Pageable host memory returns nullptr: it is staged
+// on the device and copied.
+uint32_t *direct_out(uint32_t *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) return (uint32_t *)at.devicePointer;
+    return nullptr;
+}
+
 void release_work_arrays(kairos_graph *g) {
     auto &w = g->work;
     const auto &A = g->A;
@@ -220,6 +235,11 @@ EdgeMapArgs make_args(kairos_graph *g, const Csr &c, const LaneParams &lp, uint3
     a.warp_max_edges = g->tuning.warp_max_edges;
     a.chunk_edges = g->tuning.chunk_edges;
     a.dense_div = g->tuning.dense_div;
+    a.hidx = c.hidx;
+    a.hhdr = c.hhdr;
+    a.hcum = c.hcum;
+    a.hrow = c.hrow;
+    a.select_permille = c.hidx ? g->tuning.select_permille : 0;
     a.count_relaxed = count_relaxed;
     a.relax_mode = g->tuning.relax_mode;
     a.resume = 0;
@@ -269,6 +289,313 @@ void drop_graph(kairos_graph *g) {
     cudaGetLastError();
 }
 
+// ---- stream mode (relax_mode 3) -------------------------------------------------------------
+
+void release_stream_work(kairos_graph *g) {
+    for (auto &sw : g->sw) {
+        g->A.put(sw.arr);
+        g->A.put(sw.minrow);
+        g->A.put(sw.rmax);
+        g->A.put(sw.rmask);
+        g->A.put(sw.fbm);
+        g->A.put(sw.fq);
+        sw = kairos_graph::StreamWork();
+    }
+}
+
+int64_t default_block_edges(const kairos_graph *g) {
+    if (g->tuning.block_edges > 0) return g->tuning.block_edges;
+    return std::max<int64_t>(g->m / 512, 4096);
+}
+
+// The time-ordered records of the directions the call needs, cut for the current block size.
+kairos_status ensure_time_stream(kairos_graph *g, bool fwd, bool rev) {
+    const int64_t eb = default_block_edges(g);
+    for (int d = 0; d < 2; ++d) {
+        if (d == 0 ? !fwd : !rev) continue;
+        TimeStream &ts = d == 0 ? g->ts_fwd : g->ts_rev;
+        const Csr &c = d == 0 ? g->fwd : g->rev;
+        if (!ts.rec) {
+            ts.rec = (StreamRec *)g->A.get((size_t)std::max<int64_t>(g->m, 1) * sizeof(StreamRec));
+            if (!ts.rec) return fail(KAIROS_ERR_OOM, "time stream: device allocation failed");
+            kairos_status st = build_time_stream(g->A, g->stream, g->n, g->m, c, g->lam_bits, ts.rec);
+            if (st != KAIROS_OK) {
+                free_time_stream(g->A, &ts);
+                return st;
+            }
+        }
+        if (!ts.bnd || ts.block_edges != eb) {
+            kairos_status st = cut_time_blocks(g->A, g->stream, g->m, eb, &ts);
+            if (st != KAIROS_OK) return st;
+        }
+    }
+    return KAIROS_OK;
+}
+
+kairos_status ensure_stream_work(kairos_graph *g, int W, int slots) {
+    const int64_t n = g->n, nwords = (n + 31) / 32;
+    for (int i = 0; i < slots; ++i) {
+        auto &sw = g->sw[i];
+        if (sw.arr && sw.lanes == W) continue;
+        g->A.put(sw.arr);
+        g->A.put(sw.minrow);
+        g->A.put(sw.rmax);
+        g->A.put(sw.rmask);
+        g->A.put(sw.fbm);
+        g->A.put(sw.fq);
+        sw = kairos_graph::StreamWork();
+        sw.arr = (uint32_t *)g->A.get((size_t)n * W * 4);
+        sw.minrow = (uint32_t *)g->A.get((size_t)n * 4);
+        sw.rmax = (uint32_t *)g->A.get((size_t)n * 4);
+        sw.rmask = (unsigned long long *)g->A.get((size_t)n * 8);
+        sw.fbm = (uint32_t *)g->A.get((size_t)nwords * 4);
+        sw.fq = (int32_t *)g->A.get((size_t)n * 2 * 4);
+        if (!sw.arr || !sw.minrow || !sw.rmax || !sw.rmask || !sw.fbm || !sw.fq) {
+            release_stream_work(g);
+            return fail(KAIROS_ERR_OOM, "stream workspace: device allocation failed");
+        }
+        sw.lanes = W;
+        sw.bytes = (size_t)n * W * 4 + (size_t)n * 24 + (size_t)nwords * 4;
+    }
+    return KAIROS_OK;
+}
+
+kairos_status ensure_sctr_slots(kairos_graph *g, size_t count) {
+    if (g->sctr_slots >= count) return KAIROS_OK;
+    g->A.put(g->sctrs);
+    if (g->sctrs_host) cudaFreeHost(g->sctrs_host);
+    g->sctrs = nullptr;
+    g->sctrs_host = nullptr;
+    g->sctr_slots = 0;
+    const size_t want = std::max<size_t>(count, 8);
+    g->sctrs = (StreamCtr *)g->A.get(want * sizeof(StreamCtr));
+    if (!g->sctrs) return fail(KAIROS_ERR_OOM, "stream counters: device allocation failed");
+    KAIROS_CUDA(cudaMallocHost(&g->sctrs_host, want * sizeof(StreamCtr)), "stream counters: pinned allocation");
+    g->sctr_slots = want;
+    return KAIROS_OK;
+}
+
+kairos_status stream_error(int err) {
+    if (err == KERR_FIX_ROUNDS) return fail(KAIROS_ERR_TIMEOUT, "stream edge-map: fix-up round cap reached");
+    if (err == KERR_BARRIER_TIMEOUT) return fail(KAIROS_ERR_TIMEOUT, "stream edge-map: a grid barrier wait ran past its limit");
+    return fail(KAIROS_ERR_INTERNAL, "stream edge-map: device error");
+}
+
+struct StreamPlanned {
+    StreamArgs a;
+    std::vector<int> qid;
+    bool host_out;
+};
+
+// Queries through the time-ordered edge-map, `lanes` (32 or 64) per launch; the same contract
+// as kairos_run_queries.
+kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_t nq, uint32_t *out,
+                                 kairos_query_stats *stats, int lanes) {
+    const int64_t n = g->n;
+    uint32_t *const host_out = out;  // the caller's pointer (staged copies go there)
+    if (out) {
+        uint32_t *d = direct_out(out);
+        if (d) out = d;
+    }
+    const bool dev = out ? out != host_out || device_ptr(out) : true;
+    bool need_f = false, need_r = false;
+    int64_t n_launch = 0;
+    for (int kind = 0; kind < 2; ++kind) {
+        int64_t c = 0;
+        for (int i = 0; i < nq; ++i) c += qs[i].kind == kind;
+        n_launch += (c + lanes - 1) / lanes;
+        if (c) (kind == 0 ? need_f : need_r) = true;
+    }
+    const int C = (dev && g->tuning.concurrent >= 2 && n_launch >= 2) ? 2 : 1;
+    kairos_status st = ensure_time_stream(g, need_f, need_r);
+    if (st != KAIROS_OK) return st;
+    st = ensure_stream_work(g, lanes, C);
+    if (st != KAIROS_OK) return st;
+    auto &w = g->work;
+    if (out && !dev && !w.stage) {
+        // host outputs: rows are staged on the device and copied after each launch
+        w.stage = (uint32_t *)g->A.get((size_t)n * lanes * 4);
+        if (!w.stage) return fail(KAIROS_ERR_OOM, "stream staging: device allocation failed");
+        w.bytes += (size_t)n * lanes * 4;
+    } else if (out && !dev && w.stage && w.lanes < lanes) {
+        g->A.put(w.stage);
+        w.bytes -= (size_t)n * std::max(w.lanes, 1) * 4;
+        w.stage = (uint32_t *)g->A.get((size_t)n * lanes * 4);
+        if (!w.stage) return fail(KAIROS_ERR_OOM, "stream staging: device allocation failed");
+        w.bytes += (size_t)n * lanes * 4;
+    }
+    if (C == 2 && !w.side) {
+        KAIROS_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking), "concurrent launches: stream");
+        KAIROS_CUDA(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming), "concurrent launches: event");
+        KAIROS_CUDA(cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming), "concurrent launches: event");
+    }
+    g->last_kernel_ms = 0;
+    cudaStream_t s = g->stream;
+    std::vector<StreamPlanned> plan;
+    std::vector<int> idx;
+    uint32_t round_cap = (uint32_t)std::min<int64_t>(n + 1, 0xFFFFFFF0LL);
+    if (const char *v = getenv("KAIROS_ROUND_CAP")) round_cap = (uint32_t)strtoul(v, nullptr, 10);
+    unsigned long long spin = DEFAULT_SPIN_LIMIT;
+    if (const char *v = getenv("KAIROS_SPIN_LIMIT")) spin = strtoull(v, nullptr, 10);
+    for (int kind = 0; kind < 2; ++kind) {
+        idx.clear();
+        for (int i = 0; i < nq; ++i)
+            if (qs[i].kind == kind) idx.push_back(i);
+        const Csr &csr = kind == KAIROS_EA ? g->fwd : g->rev;
+        const TimeStream &ts = kind == KAIROS_EA ? g->ts_fwd : g->ts_rev;
+        for (size_t c = 0; c < idx.size(); c += lanes) {
+            const int k = (int)std::min<size_t>(lanes, idx.size() - c);
+            const int slot = (int)(plan.size() % C);
+            StreamPlanned P;
+            StreamArgs &a = P.a;
+            std::memset(&a, 0, sizeof(a));
+            uint32_t lo_t = INF, hi_t = 0;
+            for (int j = 0; j < k; ++j) {
+                const kairos_query &Q = qs[idx[c + j]];
+                a.lanes.src[j] = Q.vertex;
+                if (Q.kind == KAIROS_EA) {
+                    a.lanes.ta[j] = Q.ta;
+                    a.lanes.tw[j] = Q.tw;
+                } else {
+                    a.lanes.ta[j] = TMAX - Q.tw;
+                    a.lanes.tw[j] = TMAX - Q.ta;
+                    a.lanes.mirror_mask |= 1ull << j;
+                }
+                if (Q.strict) a.lanes.strict_mask |= 1ull << j;
+                a.lanes.row[j] = (out && dev) ? idx[c + j] : j;
+                lo_t = std::min(lo_t, a.lanes.ta[j]);
+                hi_t = std::max(hi_t, a.lanes.tw[j]);
+            }
+            a.lanes.nlanes = k;
+            // blocks that can hold a usable departure of some lane: [block of lo_t, block after hi_t)
+            const uint32_t *bt = ts.bt_host;
+            const int nb = ts.nblk;
+            int kb = (int)(std::upper_bound(bt, bt + nb, lo_t) - bt) - 1;
+            if (kb < 0) kb = 0;
+            int ke = (int)(std::upper_bound(bt, bt + nb, hi_t) - bt);
+            if (ke < kb) ke = kb;
+            a.rec = ts.rec;
+            a.bnd = ts.bnd;
+            a.bt = ts.bt;
+            a.k_begin = kb;
+            a.k_end = ke;
+            a.off = csr.off;
+            a.dst = csr.dst;
+            a.t = csr.t;
+            a.lam = csr.lam;
+            a.n = n;
+            const auto &sw = g->sw[slot];
+            a.arr = sw.arr;
+            a.minrow = sw.minrow;
+            a.rmax = sw.rmax;
+            a.rmask = sw.rmask;
+            a.fbm = sw.fbm;
+            a.fq[0] = sw.fq;
+            a.fq[1] = sw.fq + n;
+            a.out = out ? (dev ? out : w.stage) : nullptr;
+            a.out_stride = n;
+            a.max_fix_rounds = round_cap;
+            a.spin_limit = spin;
+            a.count_relaxed = stats != nullptr;
+            static const int phase_clock = getenv("KAIROS_PHASE_CLOCK") ? atoi(getenv("KAIROS_PHASE_CLOCK")) : 0;
+            a.phase_clock = phase_clock;
+            P.qid.assign(idx.begin() + c, idx.begin() + c + k);
+            P.host_out = out && !dev;
+            plan.push_back(std::move(P));
+        }
+    }
+    if (plan.empty()) return KAIROS_OK;
+    st = ensure_sctr_slots(g, plan.size());
+    if (st != KAIROS_OK) return st;
+    for (size_t i = 0; i < plan.size(); ++i) plan[i].a.ctr = g->sctrs + i;
+    int bps = 0;
+    int grid = stream_max_grid(lanes, g->lam_bits, g->sm_count, &bps);
+    if (grid <= 0) return fail(KAIROS_ERR_CUDA, "stream edge-map: no resident launch shape (occupancy query failed)");
+    if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
+    else if (C == 2) grid = std::max(1, bps / 2) * g->sm_count;
+
+    auto enqueue = [&](bool direct) -> kairos_status {
+        if (C == 2) {
+            KAIROS_CUDA(cudaEventRecord(w.fork, s), "concurrent launches: fork");
+            KAIROS_CUDA(cudaStreamWaitEvent(w.side, w.fork, 0), "concurrent launches: fork");
+        }
+        for (size_t i = 0; i < plan.size(); ++i) {
+            cudaStream_t si = (C == 2 && (i % 2)) ? w.side : s;
+            KAIROS_CUDA(cudaMemsetAsync(plan[i].a.ctr, 0, sizeof(StreamCtr), si), "stream edge-map counters");
+            KAIROS_CUDA(stream_launch(plan[i].a, lanes, g->lam_bits, grid, si), "stream edge-map launch");
+            if (direct && plan[i].host_out) {
+                const std::vector<int> &q = plan[i].qid;
+                for (size_t j = 0; j < q.size(); ++j)
+                    KAIROS_CUDA(cudaMemcpyAsync(host_out + (int64_t)q[j] * n, w.stage + (int64_t)j * n, (size_t)n * 4,
+                                                cudaMemcpyDeviceToHost, s),
+                                "copy labels to host");
+            }
+        }
+        if (C == 2) {
+            KAIROS_CUDA(cudaEventRecord(w.join, w.side), "concurrent launches: join");
+            KAIROS_CUDA(cudaStreamWaitEvent(s, w.join, 0), "concurrent launches: join");
+        }
+        return KAIROS_OK;
+    };
+
+    KAIROS_CUDA(cudaEventRecord(w.ev0, s), "event record");
+    const bool capturable = dev && s != nullptr && !getenv("KAIROS_NO_GRAPH");
+    bool launched = false;
+    if (capturable) {
+        std::string key("stream", 6);
+        key.append((const char *)&grid, sizeof(grid));
+        for (const StreamPlanned &P : plan) key.append((const char *)&P.a, sizeof(StreamArgs));
+        if (w.graph_exec && w.graph_key == key) {
+            KAIROS_CUDA(cudaGraphLaunch(w.graph_exec, s), "graph launch");
+            launched = true;
+            ++g->graph_launches;
+        } else {
+            drop_graph(g);
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const kairos_status est = enqueue(false);
+                const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                if (est == KAIROS_OK && ce == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&w.graph_exec, graph, 0) == cudaSuccess) {
+                    w.graph_key = key;
+                    KAIROS_CUDA(cudaGraphLaunch(w.graph_exec, s), "graph launch");
+                    launched = true;
+                    ++g->graph_launches;
+                }
+                if (graph) cudaGraphDestroy(graph);
+            }
+            cudaGetLastError();
+        }
+    }
+    if (!launched) {
+        st = enqueue(true);
+        if (st != KAIROS_OK) return st;
+    }
+    KAIROS_CUDA(cudaEventRecord(w.ev1, s), "event record");
+    KAIROS_CUDA(cudaMemcpyAsync(g->sctrs_host, g->sctrs, plan.size() * sizeof(StreamCtr), cudaMemcpyDeviceToHost, s),
+                "stream edge-map counters");
+    KAIROS_CUDA(cudaStreamSynchronize(s), "stream edge-map");
+    float ms = 0;
+    KAIROS_CUDA(cudaEventElapsedTime(&ms, w.ev0, w.ev1), "event time");
+    g->last_kernel_ms = ms;
+    g->last_launches = (int)plan.size();
+    g->last_sctr = g->sctrs_host[plan.size() - 1];
+    for (size_t i = 0; i < plan.size(); ++i) {
+        const StreamCtr &res = g->sctrs_host[i];
+        if (res.err) return stream_error(res.err);
+        if (stats) {
+            for (size_t j = 0; j < plan[i].qid.size(); ++j) {
+                kairos_query_stats &S = stats[plan[i].qid[j]];
+                S.relaxed_edges = res.relaxed[j];
+                S.scanned_edges = res.scanned;
+                S.rounds = res.blocks + res.fix_rounds;
+                S.reached = res.reached[j];
+            }
+        }
+    }
+    return KAIROS_OK;
+}
+
 }  // namespace
 
 // Shared by the public query calls, the autotuner and the server.  out == nullptr runs the
@@ -278,8 +605,18 @@ void drop_graph(kairos_graph *g) {
 // CUDA graph, which is replayed while the same call repeats.
 kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_t nq, uint32_t *out,
                                  kairos_query_stats *stats, int lanes) {
+    if (g->tuning.relax_mode == 3 && lanes >= 32) return run_stream_queries(g, qs, nq, out, stats, lanes);
+    lanes = std::min(lanes, MAX_LANES);
     const int64_t n = g->n;
-    const bool dev = out ? device_ptr(out) : true;
+    uint32_t *const host_out = out;  // the caller's pointer (staged copies go there)
+    if (out) {
+        uint32_t *d = direct_out(out);
+        if (d) out = d;
+    }
+    // page-locked host outputs are written directly, like device ones, but never serve as
+    // the one-lane label array (its atomics would cross the CPU-GPU link)
+    const bool pinned = out && out != host_out;
+    const bool dev = out ? pinned || device_ptr(out) : true;
     // launches kept in flight together: two (second workspace and stream) when asked for, the
     // outputs are device memory and the call has at least two launches
     int64_t n_launch = 0;
@@ -318,8 +655,8 @@ kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs
             const uint32_t *host_src = nullptr;
             const int slot = (int)(plan.size() % C);
             if (lanes == 1) {
-                alias = (out && dev) ? out + (int64_t)idx[c] * n : (slot ? w.arr2 : w.arr);
-                o = out ? alias : nullptr;
+                alias = (out && dev && !pinned) ? out + (int64_t)idx[c] * n : (slot ? w.arr2 : w.arr);
+                o = out ? (pinned ? out + (int64_t)idx[c] * n : alias) : nullptr;
                 if (out && !dev) host_src = w.arr;
             } else if (out) {
                 if (dev) {
@@ -359,7 +696,7 @@ kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs
             if (direct && plan[i].host_src) {
                 const std::vector<int> &q = plan[i].qid;
                 for (size_t j = 0; j < q.size(); ++j)
-                    KAIROS_CUDA(cudaMemcpyAsync(out + (int64_t)q[j] * n, plan[i].host_src + (int64_t)j * n,
+                    KAIROS_CUDA(cudaMemcpyAsync(host_out + (int64_t)q[j] * n, plan[i].host_src + (int64_t)j * n,
                                                 (size_t)n * 4, cudaMemcpyDeviceToHost, s),
                                 "copy labels to host");
             }
@@ -469,6 +806,7 @@ kairos_status kairos_graph_build(const kairos_edge_list *el, const kairos_graph_
     };
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
+    g->device = dev;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaEventCreate(&g->work.ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&g->work.ev1);
@@ -547,6 +885,11 @@ void kairos_graph_free(kairos_graph *g) {
         cudaStreamSynchronize(g->stream);
         cudaGetLastError();
         release_work_arrays(g);
+        release_stream_work(g);
+        free_time_stream(g->A, &g->ts_fwd);
+        free_time_stream(g->A, &g->ts_rev);
+        g->A.put(g->sctrs);
+        if (g->sctrs_host) cudaFreeHost(g->sctrs_host);
         release_fastest_scratch(g);
         release_duration_scratch(g);
         free_csr(g->A, &g->fwd);
@@ -574,7 +917,9 @@ kairos_status kairos_graph_get_info(const kairos_graph *g, kairos_graph_info *in
     info->indexed_vertices = g->fwd.indexed;
     const int64_t per_dir = (g->n + 1) * 8 + g->m * (8 + (g->lam_bits == 16 ? 2 : 4));
     info->device_bytes = per_dir * (g->has_rev ? 2 : 1) + (g->fwd.n_fence + g->rev.n_fence) * 4 +
-                         (g->fwd.fidx ? g->n * 4 : 0) + (g->rev.fidx ? g->n * 4 : 0) + (int64_t)g->work.bytes;
+                         (g->fwd.fidx ? g->n * 4 : 0) + (g->rev.fidx ? g->n * 4 : 0) + (int64_t)g->work.bytes +
+                         (g->ts_fwd.rec ? g->m * 16 : 0) + (g->ts_rev.rec ? g->m * 16 : 0) + (int64_t)g->sw[0].bytes +
+                         (int64_t)g->sw[1].bytes;
     info->build_ms = g->build_ms;
     info->index_ms = g->index_ms;
     info->graph_launches = g->graph_launches;
@@ -625,15 +970,20 @@ kairos_status kairos_get_tuning(const kairos_graph *g, kairos_tuning *t) {
 kairos_status kairos_set_tuning(kairos_graph *g, const kairos_tuning *t) {
     if (!g || !t) return fail(KAIROS_ERR_INVALID_ARG, "set tuning: NULL argument");
     const int L = t->lanes;
-    if (!(L == 1 || L == 2 || L == 4 || L == 8 || L == 16 || L == 32))
-        return fail(KAIROS_ERR_INVALID_ARG, "tuning: lanes must be 1, 2, 4, 8, 16 or 32");
+    if (!(L == 1 || L == 2 || L == 4 || L == 8 || L == 16 || L == 32 || L == 64))
+        return fail(KAIROS_ERR_INVALID_ARG, "tuning: lanes must be 1, 2, 4, 8, 16, 32 or 64");
+    if (L == 64 && t->relax_mode != 3) return fail(KAIROS_ERR_INVALID_ARG, "tuning: 64 lanes need relax_mode 3");
+    if (t->relax_mode == 3 && L < 32) return fail(KAIROS_ERR_INVALID_ARG, "tuning: relax_mode 3 needs 32 or 64 lanes");
+    if (t->block_edges < 0) return fail(KAIROS_ERR_INVALID_ARG, "tuning: block_edges >= 0");
+    if (t->select_permille < 0 || t->select_permille > 1000)
+        return fail(KAIROS_ERR_INVALID_ARG, "tuning: select_permille in [0, 1000]");
     if (t->blocks_per_sm < 0 || t->blocks_per_sm > 32) return fail(KAIROS_ERR_INVALID_ARG, "tuning: blocks_per_sm in [0, 32]");
     if (t->warp_max_edges < 32 || t->warp_max_edges > (1 << 16))
         return fail(KAIROS_ERR_INVALID_ARG, "tuning: warp_max_edges in [32, 65536]");
     if (t->chunk_edges < 32 || t->chunk_edges % 32 || t->chunk_edges > (1 << 24))
         return fail(KAIROS_ERR_INVALID_ARG, "tuning: chunk_edges a multiple of 32 in [32, 2^24]");
     if (t->dense_div < 0) return fail(KAIROS_ERR_INVALID_ARG, "tuning: dense_div >= 0");
-    if (t->relax_mode < 0 || t->relax_mode > 2) return fail(KAIROS_ERR_INVALID_ARG, "tuning: relax_mode is 0, 1 or 2");
+    if (t->relax_mode < 0 || t->relax_mode > 3) return fail(KAIROS_ERR_INVALID_ARG, "tuning: relax_mode is 0, 1, 2 or 3");
     if (t->concurrent < 0 || t->concurrent > 2) return fail(KAIROS_ERR_INVALID_ARG, "tuning: concurrent is 0, 1 or 2");
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning = *t;
@@ -788,6 +1138,15 @@ int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uin
         if (ms) ms[i] = (double)(c.round_ns[i + 1] - c.round_ns[i]) * 1e-6;
     }
     return r;
+}
+
+int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out10) {
+    if (!g || !out10) return 0;
+    const StreamCtr &c = g->last_sctr;
+    const uint64_t v[10] = {c.blocks, c.fix_rounds, c.fix_vertices, c.fix_edges, c.cand, c.scanned,
+                            c.phase_cycles[0], c.phase_cycles[1], c.phase_cycles[2], c.phase_cycles[3]};
+    for (int i = 0; i < 10; ++i) out10[i] = v[i];
+    return 10;
 }
 
 int32_t kairos_last_phase_cycles(const kairos_graph *g, uint64_t *cycles8) {

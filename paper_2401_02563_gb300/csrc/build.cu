@@ -294,6 +294,131 @@ __global__ void invert_payload(int64_t m, const uint32_t *vals, uint32_t *slot) 
         slot[vals[j]] = (uint32_t)j;
 }
 
+// ---- time-ordered stream ------------------------------------------------------------------
+
+__global__ void time_keys(int64_t m, const uint32_t *t, uint64_t *keys, uint32_t *vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        keys[i] = t[i];
+        vals[i] = (uint32_t)i;
+    }
+}
+
+template <typename LamT>
+__global__ void gather_records(int64_t m, const uint32_t *vals, const int32_t *src_of, const int32_t *dst,
+                               const uint32_t *t, const LamT *lam, StreamRec *out) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t e = vals[j];
+        StreamRec r;
+        r.src = src_of[e];
+        r.dst = dst[e];
+        r.t = t[e];
+        r.lam = (uint32_t)lam[e];
+        out[j] = r;
+    }
+}
+
+// For k < nb: the block of records starting near k * eb begins at the first record departing at
+// or after rec[k * eb].t (so that no instant is split); bnd[nb] = m.
+__global__ void block_starts(const StreamRec *rec, int64_t m, int64_t eb, int64_t nb, uint64_t *bnd, uint32_t *bt) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= nb; k += (int64_t)gridDim.x * blockDim.x) {
+        if (k == nb) {
+            bnd[k] = (uint64_t)m;
+            bt[k] = INF;
+            continue;
+        }
+        const uint32_t key = rec[k * eb].t;
+        int64_t lo = 0, hi = k * eb;  // rec[hi].t == key: the answer is in [lo, hi]
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (rec[mid].t < key) lo = mid + 1; else hi = mid;
+        }
+        bnd[k] = (uint64_t)lo;
+        bt[k] = key;
+    }
+}
+
+// ---- selectivity histograms (Sec. 5.2) ------------------------------------------------------
+
+__global__ void hist_flags(int64_t n, const uint64_t *off, uint32_t min_degree, uint32_t *flag) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        flag[u] = (off[u + 1] - off[u]) >= (uint64_t)min_degree && off[u + 1] > off[u] ? 1u : 0u;
+}
+
+__global__ void hist_number(int64_t n, const uint32_t *flag, const uint32_t *pos, uint32_t *hidx, int32_t *verts) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        hidx[u] = flag[u] ? pos[u] : NO_HIST;
+        if (flag[u]) verts[pos[u]] = (int32_t)u;
+    }
+}
+
+// One block per histogram: bucket counts in shared memory, then the row-wise prefix sums.
+template <typename LamT>
+__global__ void __launch_bounds__(256) hist_fill(int64_t nh, const int32_t *verts, const uint64_t *off, const uint32_t *t,
+                                                 const LamT *lam, HistHdr *hdr, uint32_t *hcum, uint32_t *hrow) {
+    extern __shared__ uint32_t cnt[];  // HIST_B * HIST_B counts, then HIST_B row totals
+    __shared__ uint32_t lmn[8], lmx[8];
+    for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int32_t u = verts[h];
+        const uint64_t o0 = off[u], o1 = off[u + 1];
+        const uint32_t tmin = t[o0], tmax = t[o1 - 1];  // each list is in departure order
+        uint32_t mn = 0xFFFFFFFFu, mx = 0;
+        for (uint64_t e = o0 + threadIdx.x; e < o1; e += blockDim.x) {
+            const uint32_t x = (uint32_t)lam[e];
+            mn = min(mn, x);
+            mx = max(mx, x);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+            mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+        }
+        for (int i = threadIdx.x; i < HIST_B * HIST_B; i += blockDim.x) cnt[i] = 0;
+        if ((threadIdx.x & 31) == 0) {
+            lmn[threadIdx.x >> 5] = mn;
+            lmx[threadIdx.x >> 5] = mx;
+        }
+        __syncthreads();
+        mn = lmn[0];
+        mx = lmx[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            mn = min(mn, lmn[w]);
+            mx = max(mx, lmx[w]);
+        }
+        const uint64_t S = (uint64_t)tmax - tmin + 1, D = (uint64_t)mx - mn + 1;
+        for (uint64_t e = o0 + threadIdx.x; e < o1; e += blockDim.x) {
+            const uint32_t i = (uint32_t)(((uint64_t)t[e] - tmin) * HIST_B / S);
+            const uint32_t j = (uint32_t)(((uint64_t)(uint32_t)lam[e] - mn) * HIST_B / D);
+            atomicAdd(&cnt[i * HIST_B + j], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < HIST_B) {
+            uint32_t run = 0;
+            uint32_t *row = hcum + ((size_t)h * HIST_B + threadIdx.x) * HIST_B;
+            for (int j = 0; j < HIST_B; ++j) {
+                run += cnt[threadIdx.x * HIST_B + j];
+                row[j] = run;
+            }
+            cnt[HIST_B * HIST_B + threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t run = 0;
+            uint32_t *rp = hrow + (size_t)h * (HIST_B + 1);
+            for (int i = 0; i < HIST_B; ++i) {
+                rp[i] = run;
+                run += cnt[HIST_B * HIST_B + i];
+            }
+            rp[HIST_B] = run;
+            HistHdr hh;
+            hh.tmin = tmin;
+            hh.lmin = mn;
+            hh.S = S;
+            hh.D = D;
+            hdr[h] = hh;
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 kairos_status validate_edges(cudaStream_t s, int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
@@ -552,6 +677,221 @@ kairos_status build_index(const Allocator &A, cudaStream_t s, int64_t n, uint32_
     return KAIROS_OK;
 }
 
+kairos_status build_time_stream(const Allocator &A, cudaStream_t s, int64_t n, int64_t m, const Csr &c, int lam_bits,
+                                StreamRec *out) {
+    if (m <= 0) return KAIROS_OK;
+    const int64_t nb = std::max<int64_t>(cdiv(m, RS_TILE), 1);
+    const int64_t hist_n = 256 * nb;
+    int32_t *src_of = (int32_t *)A.get((size_t)m * 4);
+    uint64_t *k0 = (uint64_t *)A.get((size_t)m * 8);
+    uint64_t *k1 = (uint64_t *)A.get((size_t)m * 8);
+    uint32_t *v0 = (uint32_t *)A.get((size_t)m * 4);
+    uint32_t *v1 = (uint32_t *)A.get((size_t)m * 4);
+    uint32_t *hist = (uint32_t *)A.get((size_t)hist_n * 4);
+    uint32_t *offs = (uint32_t *)A.get((size_t)hist_n * 4);
+    uint32_t *tmp = (uint32_t *)A.get((size_t)scan_tmp_words(hist_n) * 4);
+    auto release_tmp = [&]() {
+        A.put(src_of); A.put(k0); A.put(k1); A.put(v0); A.put(v1); A.put(hist); A.put(offs); A.put(tmp);
+    };
+    if (!src_of || !k0 || !k1 || !v0 || !v1 || !hist || !offs || !tmp) {
+        release_tmp();
+        return fail(KAIROS_ERR_OOM, "time stream: device allocation failed");
+    }
+    const int g = grid_for(m, 256);
+    edge_sources<<<g, 256, 0, s>>>(n, m, c.off, src_of);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        time_keys<<<g, 256, 0, s>>>(m, c.t, k0, v0);
+        e = cudaGetLastError();
+    }
+    // stable by departure time: equal departures keep the CSR order
+    uint64_t *ki = k0, *ko = k1;
+    uint32_t *vi = v0, *vo = v1;
+    for (int p = 0; p < 4 && e == cudaSuccess; ++p) {
+        rs_upsweep<<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, m, 8 * p, hist, nb);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = excl_scan(hist, offs, hist_n, tmp, s);
+        if (e == cudaSuccess) {
+            rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, vi, ko, vo, m, 8 * p, offs, nb);
+            e = cudaGetLastError();
+        }
+        std::swap(ki, ko);
+        std::swap(vi, vo);
+    }
+    if (e == cudaSuccess) {
+        if (lam_bits == 16)
+            gather_records<uint16_t><<<g, 256, 0, s>>>(m, vi, src_of, c.dst, c.t, (const uint16_t *)c.lam, out);
+        else
+            gather_records<uint32_t><<<g, 256, 0, s>>>(m, vi, src_of, c.dst, c.t, (const uint32_t *)c.lam, out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    release_tmp();
+    if (e != cudaSuccess) return cuda_fail(e, "time stream");
+    return KAIROS_OK;
+}
+
+void free_time_stream(const Allocator &A, TimeStream *ts) {
+    A.put(ts->rec);
+    A.put(ts->bnd);
+    A.put(ts->bt);
+    delete[] ts->bt_host;
+    *ts = TimeStream();
+}
+
+kairos_status cut_time_blocks(const Allocator &A, cudaStream_t s, int64_t m, int64_t block_edges, TimeStream *ts) {
+    A.put(ts->bnd);
+    A.put(ts->bt);
+    delete[] ts->bt_host;
+    ts->bnd = nullptr;
+    ts->bt = nullptr;
+    ts->bt_host = nullptr;
+    ts->nblk = 0;
+    const int64_t eb = std::max<int64_t>(block_edges, 1);
+    const int64_t nb = m > 0 ? cdiv(m, eb) : 0;
+    if (nb > (1 << 24)) return fail(KAIROS_ERR_INVALID_ARG, "time stream: too many blocks for this block size");
+    uint64_t *dbnd = (uint64_t *)A.get((size_t)(nb + 1) * 8);
+    uint32_t *dbt = (uint32_t *)A.get((size_t)(nb + 1) * 4);
+    if (!dbnd || !dbt) {
+        A.put(dbnd);
+        A.put(dbt);
+        return fail(KAIROS_ERR_OOM, "time stream: device allocation failed");
+    }
+    std::vector<uint64_t> hb(nb + 1);
+    std::vector<uint32_t> ht(nb + 1);
+    block_starts<<<grid_for(nb + 1, 256), 256, 0, s>>>(ts->rec, m, eb, nb, dbnd, dbt);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), dbnd, (nb + 1) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ht.data(), dbt, (nb + 1) * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        A.put(dbnd);
+        A.put(dbt);
+        return cuda_fail(e, "time stream: blocks");
+    }
+    // an instant longer than a block merges the blocks it covers: drop repeated starts
+    std::vector<uint64_t> ub;
+    std::vector<uint32_t> ut;
+    for (int64_t k = 0; k <= nb; ++k)
+        if (ub.empty() || hb[k] != ub.back()) {
+            ub.push_back(hb[k]);
+            ut.push_back(ht[k]);
+        }
+    if (ub.size() == 1 && m == 0) {  // no edges: no block
+        ub.assign(1, 0);
+        ut.assign(1, INF);
+    }
+    const int nblk = (int)ub.size() - 1;
+    e = cudaMemcpyAsync(dbnd, ub.data(), ub.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbt, ut.data(), ut.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        A.put(dbnd);
+        A.put(dbt);
+        return cuda_fail(e, "time stream: blocks");
+    }
+    ts->bnd = dbnd;
+    ts->bt = dbt;
+    ts->nblk = nblk;
+    ts->block_edges = block_edges;
+    ts->bt_host = new uint32_t[ut.size()];
+    std::copy(ut.begin(), ut.end(), ts->bt_host);
+    return KAIROS_OK;
+}
+
+void free_histograms(const Allocator &A, Csr *c) {
+    A.put(c->hidx);
+    A.put(c->hhdr);
+    A.put(c->hcum);
+    A.put(c->hrow);
+    c->hidx = nullptr;
+    c->hhdr = nullptr;
+    c->hcum = nullptr;
+    c->hrow = nullptr;
+    c->n_hist = 0;
+    c->hist_min_degree = 0;
+}
+
+kairos_status build_histograms(const Allocator &A, cudaStream_t s, int64_t n, uint32_t min_degree, int lam_bits,
+                               Csr *c) {
+    free_histograms(A, c);
+    if (min_degree == KAIROS_NO_INDEX) return KAIROS_OK;
+    if (min_degree == 0) min_degree = 1;
+    uint32_t *flag = (uint32_t *)A.get((size_t)n * 4);
+    uint32_t *pos = (uint32_t *)A.get((size_t)n * 4);
+    uint32_t *tmp = (uint32_t *)A.get((size_t)scan_tmp_words(n) * 4);
+    uint32_t *hidx = (uint32_t *)A.get((size_t)n * 4);
+    auto drop = [&]() {
+        A.put(flag);
+        A.put(pos);
+        A.put(tmp);
+    };
+    if (!flag || !pos || !tmp || !hidx) {
+        drop();
+        A.put(hidx);
+        return fail(KAIROS_ERR_OOM, "histograms: device allocation failed");
+    }
+    hist_flags<<<grid_for(n, 256), 256, 0, s>>>(n, c->off, min_degree, flag);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = excl_scan(flag, pos, n, tmp, s);
+    uint32_t last[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last[0], pos + (n - 1), 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last[1], flag + (n - 1), 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        drop();
+        A.put(hidx);
+        return cuda_fail(e, "histograms");
+    }
+    const int64_t nh = (int64_t)last[0] + last[1];
+    int32_t *verts = (int32_t *)A.get((size_t)std::max<int64_t>(nh, 1) * 4);
+    HistHdr *hdr = (HistHdr *)A.get((size_t)std::max<int64_t>(nh, 1) * sizeof(HistHdr));
+    uint32_t *hcum = (uint32_t *)A.get((size_t)std::max<int64_t>(nh, 1) * HIST_B * HIST_B * 4);
+    uint32_t *hrow = (uint32_t *)A.get((size_t)std::max<int64_t>(nh, 1) * (HIST_B + 1) * 4);
+    if (!verts || !hdr || !hcum || !hrow) {
+        drop();
+        A.put(hidx);
+        A.put(verts);
+        A.put(hdr);
+        A.put(hcum);
+        A.put(hrow);
+        return fail(KAIROS_ERR_OOM, "histograms: device allocation failed (lower the degree cutoff's count)");
+    }
+    hist_number<<<grid_for(n, 256), 256, 0, s>>>(n, flag, pos, hidx, verts);
+    e = cudaGetLastError();
+    const size_t smem = (size_t)(HIST_B * HIST_B + HIST_B) * 4;
+    if (e == cudaSuccess && nh > 0) {
+        const unsigned g = (unsigned)std::min<int64_t>(nh, 65535);
+        if (lam_bits == 16) {
+            e = cudaFuncSetAttribute(hist_fill<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                hist_fill<uint16_t><<<g, 256, smem, s>>>(nh, verts, c->off, c->t, (const uint16_t *)c->lam, hdr, hcum, hrow);
+        } else {
+            e = cudaFuncSetAttribute(hist_fill<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                hist_fill<uint32_t><<<g, 256, smem, s>>>(nh, verts, c->off, c->t, (const uint32_t *)c->lam, hdr, hcum, hrow);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    drop();
+    A.put(verts);
+    if (e != cudaSuccess) {
+        A.put(hidx);
+        A.put(hdr);
+        A.put(hcum);
+        A.put(hrow);
+        return cuda_fail(e, "histograms");
+    }
+    c->hidx = hidx;
+    c->hhdr = hdr;
+    c->hcum = hcum;
+    c->hrow = hrow;
+    c->n_hist = nh;
+    c->hist_min_degree = min_degree;
+    return KAIROS_OK;
+}
+
 void free_index(const Allocator &A, Csr *c) {
     A.put(c->fidx);
     A.put(c->fence);
@@ -563,6 +903,7 @@ void free_index(const Allocator &A, Csr *c) {
 
 void free_csr(const Allocator &A, Csr *c) {
     free_index(A, c);
+    free_histograms(A, c);
     A.put(c->off);
     A.put(c->dst);
     A.put(c->t);

@@ -48,6 +48,18 @@ struct Allocator {
     void put(void *p) const;
 };
 
+// Selectivity histogram of one vertex (Sec. 5.2): its edges' starts span [tmin, tmin + S) and
+// durations [lmin, lmin + D), each cut into HIST_B equal buckets; bucket (i, j) holds the edges
+// with (t - tmin) * HIST_B / S == i and (lam - lmin) * HIST_B / D == j.  Stored as row-wise
+// inclusive prefix sums over j (cum[i][j] = edges in buckets (i, 0..j)) and the prefix of the
+// row totals (row[i] = edges in rows 0..i-1).
+constexpr int HIST_B = 100;
+constexpr uint32_t NO_HIST = 0xFFFFFFFFu;
+struct HistHdr {
+    uint32_t tmin, lmin;
+    uint64_t S, D;
+};
+
 // One direction of the time-sorted CSR plus its fence level.
 struct Csr {
     uint64_t *off = nullptr;   // [n + 1] edge offsets
@@ -59,6 +71,13 @@ struct Csr {
     int64_t n_fence = 0;
     int64_t indexed = 0;
     int64_t max_deg = 0;
+    // selectivity histograms of the vertices with degree >= hist_min_degree
+    uint32_t *hidx = nullptr;  // [n] histogram number of the vertex, NO_HIST if none
+    HistHdr *hhdr = nullptr;   // [n_hist]
+    uint32_t *hcum = nullptr;  // [n_hist][HIST_B][HIST_B]
+    uint32_t *hrow = nullptr;  // [n_hist][HIST_B + 1]
+    int64_t n_hist = 0;
+    uint32_t hist_min_degree = 0;
 };
 
 // Counters of one persistent edge-map launch (zeroed before each launch).  Counters that
@@ -152,7 +171,110 @@ struct EdgeMapArgs {
     uint32_t running_mask;
     int phase_clock;       // nonzero: accumulate per-phase cycle counts (diagnostics)
     unsigned long long spin_limit;  // polls before a device wait gives up (KERR_*_TIMEOUT)
+    // per-vertex access choice (Sec. 5.1, Eq. 3): for a vertex with a histogram, scan its whole
+    // list when the estimated selectivity exceeds select_permille / 1000, else search the index
+    // (select_permille 0: the degree threshold alone decides)
+    const uint32_t *hidx;
+    const HistHdr *hhdr;
+    const uint32_t *hcum;
+    const uint32_t *hrow;
+    int select_permille;
 };
+
+// ---- time-ordered stream mode (relax_mode 3) ---------------------------------------------
+//
+// Every edge of one direction as a 16-byte record in ascending departure time (ties in edge
+// order), cut into time blocks: block k holds the records [bnd[k], bnd[k+1]), all departing in
+// [bt[k], bt[k+1]) (an instant is never split).  A launch sweeps the blocks in time order;
+// edges inside a block are relaxed together, and chains that start and end inside one block
+// are finished by frontier rounds restricted to the block ("fix-ups").
+constexpr int STREAM_MAX_LANES = 64;
+struct StreamRec {
+    int32_t src, dst;
+    uint32_t t, lam;
+};
+struct TimeStream {
+    StreamRec *rec = nullptr;  // [m]
+    uint64_t *bnd = nullptr;   // [nblk + 1] first record of each block; bnd[nblk] = m
+    uint32_t *bt = nullptr;    // [nblk + 1] first departure of each block; bt[nblk] = INF
+    int32_t nblk = 0;
+    int64_t block_edges = 0;   // target records per block the cut was made for
+    uint32_t *bt_host = nullptr;  // host copy of bt
+};
+
+enum : int { KERR_FIX_ROUNDS = 5 };
+
+struct StreamLanes {
+    int32_t src[STREAM_MAX_LANES];
+    uint32_t ta[STREAM_MAX_LANES];
+    uint32_t tw[STREAM_MAX_LANES];
+    int64_t row[STREAM_MAX_LANES];     // output row of lane q
+    unsigned long long strict_mask;    // bit q: StrictlySucceeds
+    unsigned long long mirror_mask;    // bit q: output is KAIROS_TIME_MAX - label
+    int32_t nlanes;
+};
+
+struct StreamCtr {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int err;
+    unsigned int pad0[29];
+    PaddedU32 fcount[3];  // fix-up queue lengths, by generation mod 3
+    PaddedU32 fnext[3];   // fix-up vertices claimed, by generation mod 3
+    unsigned long long scanned;     // stream records read plus fix-up edges read
+    unsigned long long cand;        // records whose lanes were examined
+    unsigned long long fix_edges;   // edges read by fix-ups
+    unsigned long long fix_vertices;
+    unsigned int fix_rounds;        // fix-up generations run
+    unsigned int blocks;            // time blocks swept
+    // SM cycles summed over warps when StreamArgs::phase_clock is set: 0 block passes,
+    // 1 fix-ups, 2 grid barriers, 3 initialisation and read-out
+    unsigned long long phase_cycles[4];
+    unsigned long long relaxed[STREAM_MAX_LANES];
+    unsigned int reached[STREAM_MAX_LANES];
+};
+
+struct StreamArgs {
+    const StreamRec *rec;
+    const uint64_t *bnd;
+    const uint32_t *bt;
+    int32_t k_begin, k_end;  // blocks swept
+    // the same direction as a time-sorted CSR (fix-ups walk one vertex's list)
+    const uint64_t *off;
+    const int32_t *dst;
+    const uint32_t *t;
+    const void *lam;
+    int64_t n;
+    uint32_t *arr;     // [n][W] labels
+    uint32_t *minrow;  // [n] at most the least label of the vertex over the lanes
+    unsigned long long *rmask;  // [n] lanes in which the vertex has a finite label (may lag, never ahead)
+    uint32_t *rmax;    // [n] at least every label of the vertex in a lane of rmask (raised before a
+                       // lane joins rmask, so a reader that sees the lane sees the bound)
+    uint32_t *fbm;     // fix-up dedupe bitmap, ceil(n/32) words (all clear between blocks)
+    int32_t *fq[2];    // fix-up queues, n entries each
+    StreamCtr *ctr;
+    uint32_t *out;     // out[row_q * out_stride + v]; nullptr: none
+    int64_t out_stride;
+    StreamLanes lanes;
+    uint32_t max_fix_rounds;  // per block; past it KERR_FIX_ROUNDS
+    unsigned long long spin_limit;
+    int count_relaxed;        // nonzero: count usable edges per lane under the final labels
+    int phase_clock;          // nonzero: accumulate per-phase cycle counts (diagnostics)
+};
+
+// Launch one stream-mode edge-map of W in {32, 64} lanes (cooperative).
+cudaError_t stream_launch(const StreamArgs &a, int W, int lam_bits, int grid, cudaStream_t s);
+int stream_max_grid(int W, int lam_bits, int sm_count, int *blocks_per_sm_out);
+template <int W>
+cudaError_t stream_launch_w(const StreamArgs &a, int lam_bits, int grid, cudaStream_t s);
+template <int W>
+int stream_max_blocks_w(int lam_bits);
+// Build the time-ordered records of one direction from its CSR, and cut them into blocks of
+// about block_edges records.
+kairos_status build_time_stream(const Allocator &A, cudaStream_t s, int64_t n, int64_t m, const Csr &c, int lam_bits,
+                                StreamRec *out);
+kairos_status cut_time_blocks(const Allocator &A, cudaStream_t s, int64_t m, int64_t block_edges, TimeStream *ts);
+void free_time_stream(const Allocator &A, TimeStream *ts);
 
 // Between resumable launches (serving): column operations on the [n][W] state.
 // Retire the lanes in mask in one pass over the vertices: lanes in write_mask get
@@ -186,6 +308,8 @@ int edgemap_max_blocks_w(int lam_bits, int relax_mode);
 // calls, the autotuner and fastest paths).  out == nullptr discards the labels.
 kairos_status kairos_run_queries(kairos_graph *g, const kairos_query *qs, int32_t nq, uint32_t *out,
                                  kairos_query_stats *stats, int lanes);
+// The device a server's graph lives on (serve.cpp; used by the router).
+int kairos_server_device(const kairos_server *s);
 // Free the fastest-path scratch of a graph (fastest.cu).
 void release_fastest_scratch(kairos_graph *g);
 // Free the shortest-duration state of a graph (duration.cu).
@@ -206,6 +330,10 @@ kairos_status validate_edges(cudaStream_t s, int64_t n, int64_t m, const int32_t
                              const uint32_t *t, const void *lam, int lam_bits, int *flags_host,
                              const Allocator &A);
 kairos_status build_index(const Allocator &A, cudaStream_t s, int64_t n, uint32_t threshold, Csr *c);
+// Selectivity histograms of the vertices with degree >= min_degree (KAIROS_NO_INDEX: none).
+kairos_status build_histograms(const Allocator &A, cudaStream_t s, int64_t n, uint32_t min_degree, int lam_bits,
+                               Csr *c);
+void free_histograms(const Allocator &A, Csr *c);
 void free_index(const Allocator &A, Csr *c);
 void free_csr(const Allocator &A, Csr *c);
 // Count vertices with degree > x and the grid chunks their full ranges need.
@@ -217,6 +345,7 @@ kairos_status split_capacity(const Allocator &A, cudaStream_t s, int64_t n, cons
 // The graph object behind the opaque C handle.
 struct kairos_graph {
     int64_t n = 0, m = 0;
+    int device = 0;  // the device current at build: every call on the graph uses it
     int lam_bits = 32;
     cudaStream_t stream = nullptr;
     kairos::Allocator A;
@@ -265,6 +394,19 @@ struct kairos_graph {
         void *sd_chunks = nullptr;                  // relaxation work items
         unsigned long long *sd_ctr = nullptr, *sd_ctr_host = nullptr;
     } work;
+    // time-ordered stream mode: records per direction (built on first use) and the launch
+    // workspace (two sets when two launches are in flight)
+    kairos::TimeStream ts_fwd, ts_rev;
+    struct StreamWork {
+        int lanes = 0;
+        uint32_t *arr = nullptr, *minrow = nullptr, *rmax = nullptr, *fbm = nullptr;
+        unsigned long long *rmask = nullptr;
+        int32_t *fq = nullptr;
+        size_t bytes = 0;
+    } sw[2];
+    kairos::StreamCtr *sctrs = nullptr, *sctrs_host = nullptr;
+    kairos::StreamCtr last_sctr{};  // counters of the last stream-mode launch (diagnostics)
+    size_t sctr_slots = 0;
     int last_launches = 0;
     int64_t graph_launches = 0;
 };

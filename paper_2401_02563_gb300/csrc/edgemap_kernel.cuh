@@ -32,6 +32,8 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "grid_sync.cuh"
+#include "hist.cuh"
 
 namespace kairos {
 namespace {
@@ -39,50 +41,8 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid-wide barrier of a cooperative launch (all blocks resident).  Every wait is bounded:
-// past the limit the block records KERR_BARRIER_TIMEOUT and leaves.  Returns true when the
-// launch may go on (no error recorded anywhere).
 __device__ __forceinline__ bool grid_sync(EdgeMapCtr *c, int *s_flag, unsigned long long limit) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned gen = ld_acquire(&c->bar_gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (ld_acquire(&c->bar_gen) == gen) {
-                if (++spins > limit) {
-                    atomicCAS(&c->err, 0, KERR_BARRIER_TIMEOUT);
-                    break;
-                }
-                __nanosleep(128);
-            }
-        }
-        __threadfence();
-        *s_flag = __ldcg(&c->err);
-    }
-    __syncthreads();
-    return *s_flag == 0;
+    return kairos::grid_sync(c, s_flag, limit, KERR_BARRIER_TIMEOUT);
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
@@ -209,6 +169,7 @@ struct LaneReg {
 struct BlockSmem {
     uint32_t tw[MAX_LANES];   // window end per lane
     uint32_t cnt[MAX_LANES];  // relaxations per lane (lanes > 1)
+    uint32_t twmax;           // latest window end over the launch's lanes
     int flag;
 };
 
@@ -580,7 +541,18 @@ __device__ __forceinline__ void expand(const EdgeMapArgs &a, WarpSmem<W> &S, Blo
         const uint32_t deg = (uint32_t)(__ldg(&a.off[u + 1]) - o0);
         const uint32_t fi = a.fidx ? __ldg(&a.fidx[u]) : NO_FENCE;
         uint32_t lo = 0, hi = deg;
-        if (fi != NO_FENCE) lower_bound2_fenced(a.t + o0, deg, a.fence + fi, Lm, Hm, lo, hi);
+        bool search = fi != NO_FENCE;
+        if (search && a.select_permille > 0 && a.hidx) {
+            // Eq. 3: search the index when the estimated selectivity of the departure interval
+            // (and the latest window end) is at most theta_sel, else scan the whole list
+            const uint32_t hx = __ldg(&a.hidx[u]);
+            if (hx != NO_HIST) {
+                const uint64_t k = hist_estimate(a.hhdr[hx], a.hcum + (size_t)hx * HIST_B * HIST_B, Lm, (uint64_t)Hm - 1,
+                                                 B.twmax);
+                search = 1000ull * k <= (uint64_t)a.select_permille * deg;
+            }
+        }
+        if (search) lower_bound2_fenced(a.t + o0, deg, a.fence + fi, Lm, Hm, lo, hi);
         len = hi - lo;
         base = o0 + lo;
     }
@@ -691,6 +663,12 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 || W == 16) ? 4 : (W == 32
         B.tw[threadIdx.x] = a.lanes.tw[threadIdx.x];
         B.cnt[threadIdx.x] = 0;
     }
+    if (threadIdx.x == 0) {
+        uint32_t m = 0;
+        for (int q = 0; q < a.lanes.nlanes; ++q) m = max(m, a.lanes.tw[q]);
+        B.twmax = m;
+    }
+    __syncthreads();  // the block's lane constants are read by every warp
     unsigned long long cnt1 = 0, scanned = 0;
     unsigned reached = 0;
     PhaseClock pc;
@@ -924,10 +902,39 @@ __global__ void __launch_bounds__(EM_THREADS, (W == 1 || W == 16) ? 4 : (W == 32
         const size_t v = i / W;
         const uint32_t x = __ldcg(&a.arr[i]);
         reached += (x != INF);
-        if (a.out) {
+        if (a.out && W == 1) {
             const bool mir = (a.lanes.mirror_mask >> R.q) & 1u;
             const uint32_t y = (mir && x != INF) ? TMAX - x : x;
             if (!(a.out_is_arr && !mir)) a.out[a.lanes.row[R.q] * a.out_stride + (int64_t)v] = y;
+        }
+    }
+    if (W > 1 && a.out && !a.resume) {
+        // several lanes: 32 vertices x W lanes at a time through shared memory (the rounds are
+        // over, so the warps' scratch is free once their phase sums are out), so that both the
+        // [n][W] state and the output rows move in whole segments, also when the output is
+        // host memory
+        pc.mark(7);
+        if (pc.on && lane == 0)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) atomicAdd(&C->phase_cycles[i], S.phase[i]);
+        pc.on = false;
+        uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);
+        const int64_t ntile = (n + 31) / 32;
+        for (int64_t tl = blockIdx.x; tl < ntile; tl += gridDim.x) {
+            const int64_t v0 = tl * 32;
+            const int nv = (int)(n - v0 < 32 ? n - v0 : 32);
+            __syncthreads();
+            for (int i = threadIdx.x; i < nv * W; i += EM_THREADS)
+                tile[(i / W) * (W + 1) + i % W] = __ldcg(&a.arr[(size_t)v0 * W + i]);
+            __syncthreads();
+            for (int i = threadIdx.x; i < 32 * W; i += EM_THREADS) {
+                const int q = i >> 5, vv = i & 31;
+                if (q < a.lanes.nlanes && ((a.running_mask >> q) & 1u) && vv < nv) {
+                    const uint32_t x = tile[vv * (W + 1) + q];
+                    const bool mir = (a.lanes.mirror_mask >> q) & 1u;
+                    a.out[a.lanes.row[q] * a.out_stride + v0 + vv] = (mir && x != INF) ? TMAX - x : x;
+                }
+            }
         }
     }
     // ---- counters ----

@@ -73,6 +73,7 @@ struct Session {
 
 struct kairos_server {
     kairos_graph *g = nullptr;
+    int device = 0;  // the graph's device: the worker thread runs there
     int slots = 16;
     int capacity = 4096;
     int64_t reserve = 256LL << 20;
@@ -184,7 +185,8 @@ EdgeMapArgs session_args(kairos_graph *g, Session &S) {
     a.count_relaxed = 1;
     // resumable slices keep the queue frontier, so the bitmap-frontier mode (1) is replaced
     // by the all-segment mode (0); otherwise the graph's tuned mode applies
-    a.relax_mode = g->tuning.relax_mode == 1 ? 0 : g->tuning.relax_mode;
+    // resumable slices run the frontier kernel: modes 1 and 3 relax with mode 0 there
+    a.relax_mode = (g->tuning.relax_mode == 1 || g->tuning.relax_mode == 3) ? 0 : g->tuning.relax_mode;
     a.running_mask = S.running;
     return a;
 }
@@ -338,6 +340,7 @@ kairos_status finish_session(kairos_server *V, Session &S, std::vector<std::pair
 }
 
 void worker(kairos_server *V) {
+    cudaSetDevice(V->device);  // a new thread starts on device 0
     std::vector<std::pair<uint64_t, kairos_result_info>> done;
     int turn = 0;
     for (;;) {
@@ -412,6 +415,12 @@ void worker(kairos_server *V) {
     }
 }
 
+}  // namespace
+
+int kairos::kairos_server_device(const kairos_server *V) { return V ? V->device : -1; }
+
+namespace {
+
 bool device_ptr(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -430,6 +439,7 @@ kairos_status kairos_serve_create(kairos_graph *g, const kairos_serve_opts *opts
     kairos_server *V = new (std::nothrow) kairos_server();
     if (!V) return fail(KAIROS_ERR_OOM, "serve create: host allocation failed");
     V->g = g;
+    V->device = g->device;
     if (opts) {
         if (opts->max_slots < 0 || opts->queue_capacity < 0 || opts->reserve_bytes < 0 || opts->rounds_per_slice < 0) {
             delete V;

@@ -1,0 +1,552 @@
+// The temporal edge-map in time order (relax_mode 3): a dense form of the TemporalEdgeMap
+// (Table 2, Sec. 4.4) for batches of W = 32 or 64 earliest-arrival lanes, one persistent
+// cooperative launch.
+//
+// The edges of one direction are kept as 16-byte records (tail, head, departure t,
+// duration) in ascending departure time and cut into time blocks.  The launch sweeps the
+// blocks in order.  Within block k (departures in [T_k, T_{k+1})):
+//   pass:    every record is read once, coalesced.  A record (u, v, t, lam) is relaxed in
+//            lane q when u's label in q is at most t (below t under StrictlySucceeds, except
+//            at the lane's source) and t + lam <= tw_q: arr[v][q] = min(arr[v][q], t + lam)
+//            (Alg. 2's Update).  Per-vertex summaries skip most records without touching the
+//            W-lane label rows: minrow[u] <= every label of u (a record with t < minrow[u] is
+//            usable in no lane), rmask[.] the lanes in which a vertex is reached, and rmax[v]
+//            >= every label of v in those lanes.  A record can only improve v in a lane where
+//            u is reached and either v is not (yet) or t + lam < rmax[v].
+//   fix-ups: a label that drops to a time x < T_{k+1} during the block may make records of
+//            the same block usable after the pass already read them.  Such vertices form a
+//            frontier; each round relaxes their out-edges departing in [x, T_{k+1}) (a binary
+//            search in the time-sorted CSR list), and heads whose labels drop below T_{k+1}
+//            form the next round's frontier, until it is empty.
+// Labels below T_k never change again (they come from edges departing before T_k), so after
+// the last block every label is the least fixpoint: the earliest arrival of the definition.
+// Every record is read once per launch and shared by all W lanes; the per-lane work is only
+// that of records that can improve a label.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "grid_sync.cuh"
+
+namespace kairos {
+namespace {
+
+constexpr int ST_THREADS = 256;
+constexpr int ST_KE = 4;  // records per thread per tile
+constexpr unsigned SFULL = 0xFFFFFFFFu;
+
+// Per-thread constants of its lanes q = lane + 32 i.
+template <int W>
+struct StreamLaneReg {
+    static constexpr int LPT = W / 32;
+    uint32_t tw[LPT];
+    int32_t src[LPT];
+    bool strict[LPT];
+    bool on[LPT];
+};
+
+// Thresholds of vertex u's lanes held by this thread: the least departure usable after u in
+// lane q (label, plus one under StrictlySucceeds away from the source), INF when u is
+// unreached or the lane is off.
+template <int W>
+__device__ __forceinline__ void lane_thresholds(const StreamArgs &a, const StreamLaneReg<W> &R, int lane, int32_t u,
+                                                uint32_t (&thr)[W / 32]) {
+#pragma unroll
+    for (int i = 0; i < W / 32; ++i) {
+        const uint32_t x = __ldcg(a.arr + (size_t)u * W + lane + 32 * i);
+        thr[i] = (R.on[i] && x != INF) ? x + ((R.strict[i] && u != R.src[i]) ? 1u : 0u) : INF;
+    }
+}
+
+constexpr int ST_G = 4;  // candidate edges a warp has in flight together
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The lanes of `lanes_u` (lanes where the tail is reached) in which an edge into v arriving at
+// tau can improve v: those not yet reached at v, plus, when the arrival is below rmax[v], those
+// reached there.  rmask[v] is read with acquire so that rmax[v] covers every lane it shows.
+__device__ __forceinline__ unsigned long long may_improve(const StreamArgs &a, unsigned long long lanes_u, int32_t v,
+                                                          uint32_t tau) {
+    const unsigned long long lv = ld_acquire64(&a.rmask[v]);
+    const unsigned long long fresh = lanes_u & ~lv, known = lanes_u & lv;
+    return fresh | ((known && tau < __ldcg(&a.rmax[v])) ? known : 0ull);
+}
+
+// Relax up to ST_G edges g < cnt (into head v[g], departure t[g], arrival tau[g]) in every lane,
+// given each edge's tail thresholds thr[g][.]; the warp takes part as a whole.  The head rows of
+// all edges with a usable lane are loaded together, then each is lowered where the arrival is
+// earlier.  Lanes that reach v for the first time raise rmax[v] and then join rmask[v]; a drop
+// lowers minrow[v] and queues v for this block's fix-ups when the arrival is below tend.
+template <int W>
+__device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLaneReg<W> &R, int lane, int cnt,
+                                            const uint32_t (&thr)[ST_G][W / 32], const int32_t (&v)[ST_G],
+                                            const uint32_t (&t)[ST_G], const uint32_t (&tau)[ST_G],
+                                            const unsigned long long (&cm)[ST_G], uint32_t tend, int32_t *fq,
+                                            unsigned *fcount) {
+    constexpr int LPT = W / 32;
+    bool adm[ST_G][LPT];
+    unsigned anyg = 0;
+#pragma unroll
+    for (int g = 0; g < ST_G; ++g) {
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) {
+            adm[g][i] = g < cnt && ((cm[g] >> (lane + 32 * i)) & 1ull) && thr[g][i] <= t[g] && tau[g] <= R.tw[i];
+            any |= adm[g][i];
+        }
+        if (__any_sync(SFULL, any)) anyg |= 1u << g;
+    }
+    if (!anyg) return;
+    uint32_t c[ST_G][LPT];
+#pragma unroll
+    for (int g = 0; g < ST_G; ++g)
+#pragma unroll
+        for (int i = 0; i < LPT; ++i)  // only the lanes that may drop: may be stale, never below the label
+            c[g][i] = adm[g][i] ? __ldcg(a.arr + (size_t)v[g] * W + lane + 32 * i) : 0u;
+#pragma unroll
+    for (int g = 0; g < ST_G; ++g) {
+        if (!((anyg >> g) & 1u)) continue;
+        bool imp = false;
+        unsigned long long first = 0;  // lanes reaching v for the first time
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) {
+            const bool d = adm[g][i] && tau[g] < c[g][i];
+            if (d) {
+                atomicMin(a.arr + (size_t)v[g] * W + lane + 32 * i, tau[g]);  // a reduction: result unused
+                imp = true;
+            }
+            first |= (unsigned long long)__ballot_sync(SFULL, d && c[g][i] == INF) << (32 * i);
+        }
+        const bool dropped = __any_sync(SFULL, imp);
+        if (lane == 0 && dropped) {
+            if (first) {
+                atomicMax(&a.rmax[v[g]], tau[g]);
+                __threadfence();  // the bound is visible before the lanes that need it
+                atomicOr(&a.rmask[v[g]], first);
+            }
+            atomicMin(&a.minrow[v[g]], tau[g]);
+            if (tau[g] < tend) {
+                __threadfence();  // the lowered labels precede the queue entry
+                const uint32_t bit = 1u << (v[g] & 31);
+                if (!(atomicOr(&a.fbm[v[g] >> 5], bit) & bit)) fq[atomicAdd(fcount, 1u)] = v[g];
+            }
+        }
+    }
+}
+
+// First index i in [0, deg) with tl[i] >= key (deg if none): 32 pivots per step, one per
+// thread, then the last 32 candidates.  Warp-uniform arguments and result.
+__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t *__restrict__ tl, uint32_t deg, uint32_t key,
+                                                     int lane) {
+    uint32_t lo = 0, hi = deg;  // A[i] < key for i < lo; hi = deg or A[hi] >= key
+    while (hi - lo > 32) {
+        const uint32_t span = hi - lo;
+        const uint32_t p = lo + (uint32_t)(((uint64_t)span * (uint32_t)(lane + 1)) >> 5) - 1u;  // lane 31: hi - 1
+        const bool below = __ldg(&tl[p]) < key;
+        const unsigned b = __ballot_sync(SFULL, below);
+        const int c = __popc(b);  // pivots below the key form a prefix
+        const uint32_t nlo = c ? __shfl_sync(SFULL, p, c - 1) + 1u : lo;
+        const uint32_t nhi = c < 32 ? __shfl_sync(SFULL, p, c < 32 ? c : 31) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    const bool below = lo + (uint32_t)lane < hi && __ldg(&tl[lo + lane]) < key;
+    return lo + (uint32_t)__popc(__ballot_sync(SFULL, below));
+}
+
+// Candidate edges of one warp's tile (the records, or a fix-up vertex's edges, that passed
+// both bounds).
+struct StreamCand {
+    unsigned long long cm[32 * ST_KE];  // lanes in which the edge may improve its head
+    int32_t u[32 * ST_KE], v[32 * ST_KE];
+    uint32_t t[32 * ST_KE], tau[32 * ST_KE];
+};
+
+struct StreamSmem {
+    int flag;
+    uint32_t tile[32 * 65];  // readout transpose: 32 vertices x up to 64 lanes (+1 pad)
+    StreamCand cand[ST_THREADS / 32];
+};
+
+// Append this thread's flagged edge to the warp's candidate list (ballot prefix); returns the
+// new length.
+__device__ __forceinline__ int cand_push(StreamCand &L, int len, int lane, unsigned long long cm, int32_t u, int32_t v,
+                                         uint32_t t, uint32_t tau) {
+    const bool c = cm != 0ull;
+    const unsigned m = __ballot_sync(SFULL, c);
+    if (c) {
+        const int pos = len + __popc(m & ((1u << lane) - 1u));
+        L.cm[pos] = cm;
+        L.u[pos] = u;
+        L.v[pos] = v;
+        L.t[pos] = t;
+        L.tau[pos] = tau;
+    }
+    return len + __popc(m);
+}
+
+template <int W, typename LamT>
+__global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs a) {
+    constexpr int LPT = W / 32;
+    __shared__ StreamSmem S;
+    const int lane = threadIdx.x & 31;
+    const size_t tid = (size_t)blockIdx.x * ST_THREADS + threadIdx.x;
+    const size_t nthr = (size_t)gridDim.x * ST_THREADS;
+    const unsigned gw = (unsigned)(tid >> 5), nwarps = (unsigned)(nthr >> 5);
+    const int64_t n = a.n;
+    const size_t nwords = (size_t)((n + 31) >> 5);
+    StreamCtr *C = a.ctr;
+    const LamT *__restrict__ lam = (const LamT *)a.lam;
+
+    StreamLaneReg<W> R;
+    uint32_t twmax = 0;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        const int q = lane + 32 * i;
+        R.on[i] = q < a.lanes.nlanes;
+        R.tw[i] = R.on[i] ? a.lanes.tw[q] : 0u;
+        R.src[i] = a.lanes.src[q];
+        R.strict[i] = (a.lanes.strict_mask >> q) & 1ull;
+    }
+    for (int q = 0; q < a.lanes.nlanes; ++q) twmax = max(twmax, a.lanes.tw[q]);
+
+    // ---- initial labels (Alg. 2: t[x] = window start, every other label infinite) ----
+    for (size_t i = tid; i < (size_t)n * W; i += nthr) a.arr[i] = INF;
+    for (size_t i = tid; i < (size_t)n; i += nthr) {
+        a.minrow[i] = INF;
+        a.rmask[i] = 0ull;
+        a.rmax[i] = 0u;
+    }
+    for (size_t i = tid; i < nwords; i += nthr) a.fbm[i] = 0u;
+    if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
+    if (blockIdx.x == 0 && threadIdx.x < (unsigned)a.lanes.nlanes) {
+        const int q = threadIdx.x;
+        a.arr[(size_t)a.lanes.src[q] * W + q] = a.lanes.ta[q];
+        atomicMin(&a.minrow[a.lanes.src[q]], a.lanes.ta[q]);
+        atomicMax(&a.rmax[a.lanes.src[q]], a.lanes.ta[q]);
+        atomicOr(&a.rmask[a.lanes.src[q]], 1ull << q);
+    }
+    if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
+
+    unsigned long long scanned = 0, cand = 0, fixe = 0, fixv = 0;
+    unsigned gen = 0, fix_rounds = 0;
+    unsigned long long ph[4] = {0, 0, 0, 0};
+    long long ph_last = a.phase_clock ? clock64() : 0;
+    auto mark = [&](int p) {
+        if (a.phase_clock) {
+            const long long now = clock64();
+            ph[p] += (unsigned long long)(now - ph_last);
+            ph_last = now;
+        }
+    };
+    mark(3);
+    for (int k = a.k_begin; k < a.k_end; ++k) {
+        const uint64_t lo = a.bnd[k], hi = a.bnd[k + 1];
+        const uint32_t tbeg = a.bt[k], tend = a.bt[k + 1];
+        // ---- pass: every record of the block once, KE per thread, coalesced ----
+        {
+            int32_t *fq = a.fq[gen & 1];
+            unsigned *fcount = &C->fcount[gen % 3].v;
+            for (uint64_t tb = lo + (uint64_t)gw * (32 * ST_KE); tb < hi; tb += (uint64_t)nwarps * (32 * ST_KE)) {
+                StreamRec r[ST_KE];
+                bool c[ST_KE];
+#pragma unroll
+                for (int j = 0; j < ST_KE; ++j) {
+                    const uint64_t e = tb + (uint64_t)(j * 32 + lane);
+                    c[j] = e < hi;
+                    if (c[j]) {
+                        const int4 x = __ldcs(reinterpret_cast<const int4 *>(a.rec + e));  // read once: streaming
+                        r[j].src = x.x;
+                        r[j].dst = x.y;
+                        r[j].t = (uint32_t)x.z;
+                        r[j].lam = (uint32_t)x.w;
+                        ++scanned;
+                    } else {
+                        r[j].src = r[j].dst = 0;
+                        r[j].t = r[j].lam = 0;
+                    }
+                }
+                uint32_t mn[ST_KE];
+                unsigned long long lu[ST_KE];
+#pragma unroll
+                for (int j = 0; j < ST_KE; ++j) {
+                    mn[j] = c[j] ? __ldcg(&a.minrow[r[j].src]) : INF;
+                    lu[j] = c[j] ? __ldcg(&a.rmask[r[j].src]) : 0ull;
+                }
+                StreamCand &L = S.cand[threadIdx.x >> 5];
+                int len = 0;
+#pragma unroll
+                for (int j = 0; j < ST_KE; ++j) {
+                    const uint32_t tau = r[j].t + r[j].lam;
+                    const bool ok = c[j] && r[j].t >= mn[j] && tau <= twmax && lu[j] != 0ull;
+                    len = cand_push(L, len, lane, ok ? may_improve(a, lu[j], r[j].dst, tau) : 0ull, r[j].src, r[j].dst,
+                                    r[j].t, tau);
+                }
+                __syncwarp();
+                cand += (lane == 0) ? len : 0;
+                for (int base = 0; base < len; base += ST_G) {
+                    const int cnt = min(ST_G, len - base);
+                    int32_t u[ST_G], v[ST_G];
+                    uint32_t t[ST_G], tau[ST_G], thr[ST_G][LPT];
+                    unsigned long long cm[ST_G];
+#pragma unroll
+                    for (int g = 0; g < ST_G; ++g) {
+                        const int k2 = base + (g < cnt ? g : 0);
+                        cm[g] = g < cnt ? L.cm[k2] : 0ull;
+                        u[g] = L.u[k2];
+                        v[g] = L.v[k2];
+                        t[g] = L.t[k2];
+                        tau[g] = L.tau[k2];
+                    }
+#pragma unroll
+                    for (int g = 0; g < ST_G; ++g)  // the tails' labels in the candidate lanes, all in flight together
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i)
+                            thr[g][i] = ((cm[g] >> (lane + 32 * i)) & 1ull) ? __ldcg(a.arr + (size_t)u[g] * W + lane + 32 * i)
+                                                                            : INF;
+#pragma unroll
+                    for (int g = 0; g < ST_G; ++g)
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) {
+                            const uint32_t x = thr[g][i];
+                            thr[g][i] = (R.on[i] && x != INF) ? x + ((R.strict[i] && u[g] != R.src[i]) ? 1u : 0u) : INF;
+                        }
+                    relax_batch<W>(a, R, lane, cnt, thr, v, t, tau, cm, tend, fq, fcount);
+                }
+                __syncwarp();
+            }
+        }
+        mark(0);
+        if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
+        mark(2);
+        // ---- fix-ups: frontier rounds over the block's departures ----
+        for (unsigned round = 0;; ++round) {
+            const unsigned F = __ldcg(&C->fcount[gen % 3].v);
+            if (F == 0) break;
+            if (round >= a.max_fix_rounds) {
+                if (tid == 0) atomicCAS(&C->err, 0, KERR_FIX_ROUNDS);
+                return;
+            }
+            if (tid == 0) {
+                C->fcount[(gen + 2) % 3].v = 0;
+            }
+            ++fix_rounds;
+            const int32_t *cq = a.fq[gen & 1];
+            int32_t *nq = a.fq[(gen + 1) & 1];
+            unsigned *ncount = &C->fcount[(gen + 1) % 3].v;
+            StreamCand &L = S.cand[threadIdx.x >> 5];
+            for (unsigned idx = gw; idx < F; idx += nwarps) {  // queue entries dealt to warps in turn
+                const int32_t u = __ldcg(&cq[idx]);
+                if (lane == 0) {
+                    atomicAnd(&a.fbm[u >> 5], ~(1u << (u & 31)));
+                    __threadfence();  // cleared before the labels are read: a later drop re-queues u
+                }
+                __syncwarp();
+                ++fixv;
+                uint32_t tu[LPT];
+                lane_thresholds<W>(a, R, lane, u, tu);
+                uint32_t tmin = INF;
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) tmin = min(tmin, tu[i]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) tmin = min(tmin, __shfl_xor_sync(SFULL, tmin, o));
+                if (tmin >= tend) continue;
+                const uint64_t o0 = __ldg(&a.off[u]);
+                const uint32_t deg = (uint32_t)(__ldg(&a.off[u + 1]) - o0);
+                // departures before the block were relaxed in every lane usable then, and a
+                // label that dropped during the block is at least its first departure
+                const uint32_t b0 = warp_lower_bound(a.t + o0, deg, max(tmin, tbeg), lane);
+                const uint32_t b1 = warp_lower_bound(a.t + o0, deg, tend, lane);
+                uint32_t thr[ST_G][LPT];
+#pragma unroll
+                for (int g = 0; g < ST_G; ++g)
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i) thr[g][i] = tu[i];
+                // lanes reached at u, from its row (exact when read)
+                unsigned long long lanes_u = 0;
+#pragma unroll
+                for (int i = 0; i < LPT; ++i)
+                    lanes_u |= (unsigned long long)__ballot_sync(SFULL, tu[i] != INF) << (32 * i);
+                for (uint32_t c0 = b0; c0 < b1; c0 += 32 * ST_KE) {
+                    int len = 0;
+#pragma unroll
+                    for (int j = 0; j < ST_KE; ++j) {
+                        const uint32_t e = c0 + j * 32 + lane;
+                        bool ok = e < b1;
+                        int32_t d = 0;
+                        uint32_t tt = 0, tau = 0;
+                        if (ok) {
+                            d = __ldg(&a.dst[o0 + e]);
+                            tt = __ldg(&a.t[o0 + e]);
+                            tau = tt + (uint32_t)__ldg(&lam[o0 + e]);
+                            ++fixe;
+                            ok = tau <= twmax;
+                        }
+                        len = cand_push(L, len, lane, ok ? may_improve(a, lanes_u, d, tau) : 0ull, u, d, tt, tau);
+                    }
+                    __syncwarp();
+                    for (int base = 0; base < len; base += ST_G) {
+                        const int cnt = min(ST_G, len - base);
+                        int32_t v[ST_G];
+                        uint32_t t[ST_G], tau[ST_G];
+                        unsigned long long cm[ST_G];
+#pragma unroll
+                        for (int g = 0; g < ST_G; ++g) {
+                            const int k2 = base + (g < cnt ? g : 0);
+                            cm[g] = g < cnt ? L.cm[k2] : 0ull;
+                            v[g] = L.v[k2];
+                            t[g] = L.t[k2];
+                            tau[g] = L.tau[k2];
+                        }
+                        relax_batch<W>(a, R, lane, cnt, thr, v, t, tau, cm, tend, nq, ncount);
+                    }
+                    __syncwarp();
+                }
+            }
+            mark(1);
+            if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
+            mark(2);
+            ++gen;
+        }
+    }
+
+    // ---- read out: out[row_q][v] = label (mirrored back for latest departure), through a
+    // shared-memory transpose so that both the label rows and the output rows move coalesced
+    if (a.out) {
+        const int64_t ntile = (n + 31) / 32;
+        for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+            const int64_t v0 = tile * 32;
+            const int nv = (int)(n - v0 < 32 ? n - v0 : 32);
+            __syncthreads();
+            for (int i = threadIdx.x; i < nv * W; i += ST_THREADS) {
+                const int vv = i / W, q = i % W;
+                S.tile[vv * (W + 1) + q] = __ldcg(a.arr + (size_t)(v0 + vv) * W + q);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < 32 * W; i += ST_THREADS) {
+                const int q = i >> 5, vv = i & 31;
+                if (q < a.lanes.nlanes && vv < nv) {
+                    const uint32_t x = S.tile[vv * (W + 1) + q];
+                    const bool mir = (a.lanes.mirror_mask >> q) & 1ull;
+                    a.out[a.lanes.row[q] * a.out_stride + v0 + vv] = (mir && x != INF) ? TMAX - x : x;
+                }
+            }
+        }
+    }
+    // ---- counters ----
+    unsigned reached[LPT];
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) reached[i] = 0;
+    for (size_t v = tid >> 5; v < (size_t)n; v += nwarps)
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) reached[i] += __ldcg(a.arr + v * W + lane + 32 * i) != INF;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i)
+        if (R.on[i] && reached[i]) atomicAdd(&C->reached[lane + 32 * i], reached[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        scanned += __shfl_xor_sync(SFULL, scanned, o);
+        fixe += __shfl_xor_sync(SFULL, fixe, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&C->scanned, scanned + fixe);
+        atomicAdd(&C->fix_edges, fixe);
+        atomicAdd(&C->cand, cand);
+        atomicAdd(&C->fix_vertices, fixv);
+    }
+    if (tid == 0) {
+        C->fix_rounds = fix_rounds;
+        C->blocks = (unsigned)(a.k_end - a.k_begin);
+    }
+    mark(3);
+    if (a.phase_clock && lane == 0)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&C->phase_cycles[p], ph[p]);
+}
+
+// Relaxed edges per lane under the final labels (the TE of the query statistics): every
+// record of the swept blocks whose tail is reached in some lane is examined lane by lane.
+template <int W>
+__global__ void __launch_bounds__(ST_THREADS) stream_count_kernel(const StreamArgs a) {
+    constexpr int LPT = W / 32;
+    __shared__ unsigned long long cnt_s[STREAM_MAX_LANES];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < STREAM_MAX_LANES) cnt_s[threadIdx.x] = 0;
+    __syncthreads();
+    StreamLaneReg<W> R;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        const int q = lane + 32 * i;
+        R.on[i] = q < a.lanes.nlanes;
+        R.tw[i] = R.on[i] ? a.lanes.tw[q] : 0u;
+        R.src[i] = a.lanes.src[q];
+        R.strict[i] = (a.lanes.strict_mask >> q) & 1ull;
+    }
+    unsigned long long cnt[LPT];
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) cnt[i] = 0;
+    const uint64_t lo = a.bnd[a.k_begin], hi = a.bnd[a.k_end];
+    const size_t tid = (size_t)blockIdx.x * ST_THREADS + threadIdx.x;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * ST_THREADS) >> 5;
+    for (uint64_t tb = lo + (tid >> 5) * 32; tb < hi; tb += nwarps * 32) {
+        const uint64_t e = tb + lane;
+        StreamRec r{0, 0, 0, 0};
+        bool c = e < hi;
+        if (c) r = a.rec[e];
+        c = c && r.t >= __ldcg(&a.minrow[r.src]);
+        unsigned m = __ballot_sync(SFULL, c);
+        while (m) {
+            const int s = __ffs(m) - 1;
+            m &= m - 1;
+            const int32_t u = __shfl_sync(SFULL, r.src, s);
+            const uint32_t t = __shfl_sync(SFULL, r.t, s);
+            const uint32_t tau = t + __shfl_sync(SFULL, r.lam, s);
+            uint32_t thr[LPT];
+            lane_thresholds<W>(a, R, lane, u, thr);
+#pragma unroll
+            for (int i = 0; i < LPT; ++i) cnt[i] += (thr[i] <= t && tau <= R.tw[i]) ? 1u : 0u;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < LPT; ++i)
+        if (cnt[i]) atomicAdd(&cnt_s[lane + 32 * i], cnt[i]);
+    __syncthreads();
+    if (threadIdx.x < (unsigned)a.lanes.nlanes && cnt_s[threadIdx.x])
+        atomicAdd(&a.ctr->relaxed[threadIdx.x], cnt_s[threadIdx.x]);
+}
+
+template <int W, typename LamT>
+cudaError_t stream_launch_t(const StreamArgs &a, int grid, cudaStream_t s) {
+    void *args[] = {(void *)&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)stream_kernel<W, LamT>, dim3(grid), dim3(ST_THREADS), args, 0, s);
+    if (e != cudaSuccess || !a.count_relaxed) return e;
+    stream_count_kernel<W><<<grid, ST_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int W, typename LamT>
+int stream_max_blocks_t() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stream_kernel<W, LamT>, ST_THREADS, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+}  // namespace
+
+template <int W>
+cudaError_t stream_launch_w(const StreamArgs &a, int lam_bits, int grid, cudaStream_t s) {
+    if (lam_bits == 16) return stream_launch_t<W, uint16_t>(a, grid, s);
+    return stream_launch_t<W, uint32_t>(a, grid, s);
+}
+
+template <int W>
+int stream_max_blocks_w(int lam_bits) {
+    return lam_bits == 16 ? stream_max_blocks_t<W, uint16_t>() : stream_max_blocks_t<W, uint32_t>();
+}
+
+}  // namespace kairos
