@@ -499,9 +499,10 @@ def reference_arm(args, rank, world):
 
 # ---- GPU measurements ------------------------------------------------------------------------
 
-def tune(torch, kx, g, queries, args, theta_default, tune_sample):
+def tune(torch, kx, g, queries, args, theta_default, tune_sample, min_lanes=1):
     """Install the launch shape: fixed by --shape / --lanes, else the autotuner (and, where the
-    workload fixes no index threshold, the threshold sweep first) on `tune_sample` queries."""
+    workload fixes no index threshold, the threshold sweep first, on `tune_sample` queries) on
+    the whole query set, over lane widths of at least min_lanes."""
     if args.shape:
         f = [int(x) for x in args.shape.split(",")]
         ln, wm, ch, dd, rm, bp = f[:6]
@@ -519,11 +520,11 @@ def tune(torch, kx, g, queries, args, theta_default, tune_sample):
         sample = ea[:k] + ld[:k]
     sweep = None
     if theta_default == kx.KAIROS_NO_INDEX:
-        # no fixed cutoff: the index threshold is tuned too (swept 16..4096)
-        g.autotune(sample)
-        best, ms = g.autotune_index(sample[: max(16, len(sample) // 2)])
-        sweep = {"best": best, "ms_by_threshold": ms}
-    g.autotune(sample)
+        # no fixed cutoff: the index threshold is tuned too (swept 16..4096), in a frontier shape
+        g.set_tuning(lanes=16, relax_mode=0, concurrent=1, block_edges=0)
+        best, ms = g.autotune_index(sample)
+        sweep = {"best": best, "ms_by_threshold": ms, "sample_queries": len(sample)}
+    g.autotune(queries, min_lanes=min_lanes)
     return sweep
 
 
@@ -641,7 +642,7 @@ def extra_batched_and_served(torch, kx, args, stream):
     with torch.cuda.stream(stream):
         g = kx.Graph.from_edges(el, stream=stream)
         g.index(16)
-        sweep = tune(torch, kx, g, qs, args, w3.theta, 64)
+        sweep = tune(torch, kx, g, qs, args, w3.theta, 64, min_lanes=8)
         b = measure_batched(torch, kx, g, el, qs, args, 1, None, stream, 3, 2, roofline=False)
         s_ms = measure_single(torch, g, qs, stream)
         res.update({"gteps": b["te_step"] / (b["step_ms"] / 1e3) / 1e9, "queries_per_s": len(qs) / (b["step_ms"] / 1e3),
@@ -728,7 +729,8 @@ def main():
         theta = w.theta if w.theta != kx.KAIROS_NO_INDEX else 16
         g.index(theta)
         info = g.info()
-        theta_sweep = tune(torch, kx, g, queries, args, w.theta, tune_sample)
+        theta_sweep = tune(torch, kx, g, queries, args, w.theta, tune_sample,
+                           min_lanes=16 if args.workload == 5 else 1)
         theta_now = (theta_sweep or {}).get("best", theta)
         b = measure_batched(torch, kx, g, el, queries, args, world, dist, stream, args.steps, args.warmup)
         step_ms, te_all = replica_reduce(b["step_ms"], b["te_step"], world, "cuda")

@@ -130,9 +130,10 @@ typedef struct {
                                queries) run mode 0 */
     int32_t concurrent;     /* launches of one call kept in flight together, each on its own stream
                                and workspace with 1/concurrent of the resident blocks (unless
-                               blocks_per_sm is set): 1 or 2 (0 means 1).  2 lets one launch's
-                               sparse final rounds overlap another's busy ones; it applies when the
-                               outputs are device memory and the call has two or more launches */
+                               blocks_per_sm is set): 1 or 2 (0 means 1), or 4 with relax_mode 3.
+                               More lets one launch's sparse rounds overlap another's busy ones; it
+                               applies when the outputs are device or page-locked host memory and
+                               the call has two or more launches */
     int32_t block_edges;    /* relax_mode 3: edges per time block (an instant is never split);
                                0: max(4096, n_edges / 512) */
     int32_t select_permille; /* selective access (Sec. 5.1, Eq. 3) for the frontier modes 0-2:
@@ -288,8 +289,17 @@ kairos_status kairos_get_tuning(const kairos_graph *g, kairos_tuning *t);
 kairos_status kairos_set_tuning(kairos_graph *g, const kairos_tuning *t);
 
 /* Time a grid of launch shapes on `sample` (its queries are run, results discarded) and
- * install the fastest; *best (may be NULL) receives it.  Errors as kairos_batch_query. */
+ * install the fastest; *best (may be NULL) receives it.  The grid covers the frontier modes
+ * (lane widths 1-32, split thresholds, queue or bitmap frontier, relaxation modes 0-2, then chunk
+ * size, resident blocks and two launches in flight) and the time-ordered mode 3 (32 and 64
+ * lanes, one, two or four launches in flight, three block sizes).  Errors as kairos_batch_query. */
 kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32_t n, kairos_tuning *best);
+
+/* The same search over lane widths of at least min_lanes only (large batches on large graphs,
+ * where narrow launches cannot win and take long to time).  Errors as kairos_autotune, and
+ * INVALID_ARG for min_lanes < 1. */
+kairos_status kairos_autotune_from(kairos_graph *g, const kairos_query *sample, int32_t n, int32_t min_lanes,
+                                   kairos_tuning *best);
 
 /* Selective-index threshold by measurement (the cost model of Sec. 5.1 sets the cutoff
  * experimentally): for each of the n_thetas candidates (KAIROS_NO_INDEX allowed) rebuild

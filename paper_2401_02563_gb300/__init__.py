@@ -119,6 +119,8 @@ SIGNATURES = {
     "kairos_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(kairos_tuning)]),
     "kairos_autotune": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32,
                                        ctypes.POINTER(kairos_tuning)]),
+    "kairos_autotune_from": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.POINTER(kairos_tuning)]),
     "kairos_autotune_index": (ctypes.c_int, [_P, ctypes.POINTER(kairos_query), ctypes.c_int32, _P, ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_uint32), _P]),
     "kairos_serve_create": (ctypes.c_int, [_P, ctypes.POINTER(kairos_serve_opts), ctypes.POINTER(_P)]),
@@ -437,10 +439,10 @@ def kairos_set_tuning(g, **fields):
     return t
 
 
-def kairos_autotune(g, sample) -> kairos_tuning:
+def kairos_autotune(g, sample, min_lanes=1) -> kairos_tuning:
     qarr, k = make_queries(sample)
     best = kairos_tuning()
-    _check(lib().kairos_autotune(g, qarr, k, ctypes.byref(best)), "kairos_autotune")
+    _check(lib().kairos_autotune_from(g, qarr, k, int(min_lanes), ctypes.byref(best)), "kairos_autotune")
     return best
 
 
@@ -642,17 +644,18 @@ class Graph:
     def set_tuning(self, **fields):
         return kairos_set_tuning(self.handle, **fields)
 
-    def autotune(self, sample, cache=None):
-        """Time launch shapes on `sample` and install the fastest.  With `cache` (a JSON file
-        path), a shape already found for this graph, index threshold, query sample, GPU model and
-        library build is installed without measuring, and a new one is stored."""
+    def autotune(self, sample, cache=None, min_lanes=1):
+        """Time launch shapes on `sample` (lane widths >= min_lanes) and install the fastest.
+        With `cache` (a JSON file path), a shape already found for this graph, index threshold,
+        query sample, GPU model and library build is installed without measuring, and a new one
+        is stored."""
         if cache is None:
-            return kairos_autotune(self.handle, sample)
-        key = autotune_cache_key(self, sample)
+            return kairos_autotune(self.handle, sample, min_lanes)
+        key = autotune_cache_key(self, sample) + (f":{min_lanes}" if min_lanes > 1 else "")
         table = _read_cache(cache)
         if key in table:
             return kairos_set_tuning(self.handle, **table[key])
-        best = kairos_autotune(self.handle, sample)
+        best = kairos_autotune(self.handle, sample, min_lanes)
         table = _read_cache(cache)  # re-read: another process may have added entries
         table[key] = {name: int(getattr(best, name)) for name, _ in kairos_tuning._fields_}
         _write_cache(cache, table)

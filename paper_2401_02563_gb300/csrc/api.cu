@@ -406,7 +406,8 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
         n_launch += (c + lanes - 1) / lanes;
         if (c) (kind == 0 ? need_f : need_r) = true;
     }
-    const int C = (dev && g->tuning.concurrent >= 2 && n_launch >= 2) ? 2 : 1;
+    const int C = dev ? (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)std::max(g->tuning.concurrent, 1), n_launch, 4}))
+                      : 1;
     kairos_status st = ensure_time_stream(g, need_f, need_r);
     if (st != KAIROS_OK) return st;
     st = ensure_stream_work(g, lanes, C);
@@ -424,11 +425,13 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
         if (!w.stage) return fail(KAIROS_ERR_OOM, "stream staging: device allocation failed");
         w.bytes += (size_t)n * lanes * 4;
     }
-    if (C == 2 && !w.side) {
-        KAIROS_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking), "concurrent launches: stream");
-        KAIROS_CUDA(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming), "concurrent launches: event");
-        KAIROS_CUDA(cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming), "concurrent launches: event");
-    }
+    if (C >= 2 && !g->sfork)
+        KAIROS_CUDA(cudaEventCreateWithFlags(&g->sfork, cudaEventDisableTiming), "concurrent launches: event");
+    for (int k = 0; k + 1 < C; ++k)
+        if (!g->sside[k]) {
+            KAIROS_CUDA(cudaStreamCreateWithFlags(&g->sside[k], cudaStreamNonBlocking), "concurrent launches: stream");
+            KAIROS_CUDA(cudaEventCreateWithFlags(&g->sjoin[k], cudaEventDisableTiming), "concurrent launches: event");
+        }
     g->last_kernel_ms = 0;
     cudaStream_t s = g->stream;
     std::vector<StreamPlanned> plan;
@@ -512,15 +515,17 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
     int grid = stream_max_grid(lanes, g->lam_bits, g->sm_count, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "stream edge-map: no resident launch shape (occupancy query failed)");
     if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
-    else if (C == 2) grid = std::max(1, bps / 2) * g->sm_count;
+    else if (C >= 2) grid = std::max(1, bps / C) * g->sm_count;  // all launches in flight resident at once
 
     auto enqueue = [&](bool direct) -> kairos_status {
-        if (C == 2) {
-            KAIROS_CUDA(cudaEventRecord(w.fork, s), "concurrent launches: fork");
-            KAIROS_CUDA(cudaStreamWaitEvent(w.side, w.fork, 0), "concurrent launches: fork");
+        if (C >= 2) {  // fork: the side streams start after everything before this call
+            KAIROS_CUDA(cudaEventRecord(g->sfork, s), "concurrent launches: fork");
+            for (int k = 0; k + 1 < C; ++k)
+                KAIROS_CUDA(cudaStreamWaitEvent(g->sside[k], g->sfork, 0), "concurrent launches: fork");
         }
         for (size_t i = 0; i < plan.size(); ++i) {
-            cudaStream_t si = (C == 2 && (i % 2)) ? w.side : s;
+            const int slot = (int)(i % C);
+            cudaStream_t si = slot ? g->sside[slot - 1] : s;
             KAIROS_CUDA(cudaMemsetAsync(plan[i].a.ctr, 0, sizeof(StreamCtr), si), "stream edge-map counters");
             KAIROS_CUDA(stream_launch(plan[i].a, lanes, g->lam_bits, grid, si), "stream edge-map launch");
             if (direct && plan[i].host_out) {
@@ -531,9 +536,9 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
                                 "copy labels to host");
             }
         }
-        if (C == 2) {
-            KAIROS_CUDA(cudaEventRecord(w.join, w.side), "concurrent launches: join");
-            KAIROS_CUDA(cudaStreamWaitEvent(s, w.join, 0), "concurrent launches: join");
+        for (int k = 0; k + 1 < C; ++k) {  // join: the call's stream waits for the side streams
+            KAIROS_CUDA(cudaEventRecord(g->sjoin[k], g->sside[k]), "concurrent launches: join");
+            KAIROS_CUDA(cudaStreamWaitEvent(s, g->sjoin[k], 0), "concurrent launches: join");
         }
         return KAIROS_OK;
     };
@@ -886,6 +891,11 @@ void kairos_graph_free(kairos_graph *g) {
         cudaGetLastError();
         release_work_arrays(g);
         release_stream_work(g);
+        for (int k = 0; k < 3; ++k) {
+            if (g->sside[k]) cudaStreamDestroy(g->sside[k]);
+            if (g->sjoin[k]) cudaEventDestroy(g->sjoin[k]);
+        }
+        if (g->sfork) cudaEventDestroy(g->sfork);
         free_time_stream(g->A, &g->ts_fwd);
         free_time_stream(g->A, &g->ts_rev);
         g->A.put(g->sctrs);
@@ -984,14 +994,20 @@ kairos_status kairos_set_tuning(kairos_graph *g, const kairos_tuning *t) {
         return fail(KAIROS_ERR_INVALID_ARG, "tuning: chunk_edges a multiple of 32 in [32, 2^24]");
     if (t->dense_div < 0) return fail(KAIROS_ERR_INVALID_ARG, "tuning: dense_div >= 0");
     if (t->relax_mode < 0 || t->relax_mode > 3) return fail(KAIROS_ERR_INVALID_ARG, "tuning: relax_mode is 0, 1, 2 or 3");
-    if (t->concurrent < 0 || t->concurrent > 2) return fail(KAIROS_ERR_INVALID_ARG, "tuning: concurrent is 0, 1 or 2");
+    if (t->concurrent < 0 || t->concurrent > 4 || t->concurrent == 3 || (t->concurrent == 4 && t->relax_mode != 3))
+        return fail(KAIROS_ERR_INVALID_ARG, "tuning: concurrent is 0, 1, 2, or 4 with relax_mode 3");
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning = *t;
     return KAIROS_OK;
 }
 
 kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32_t n, kairos_tuning *best) {
-    if (!g || !sample || n <= 0) return fail(KAIROS_ERR_INVALID_ARG, "autotune: bad argument");
+    return kairos_autotune_from(g, sample, n, 1, best);
+}
+
+kairos_status kairos_autotune_from(kairos_graph *g, const kairos_query *sample, int32_t n, int32_t min_lanes,
+                                   kairos_tuning *best) {
+    if (!g || !sample || n <= 0 || min_lanes < 1) return fail(KAIROS_ERR_INVALID_ARG, "autotune: bad argument");
     for (int i = 0; i < n; ++i) {
         kairos_status st = check_query(g, sample[i]);
         if (st != KAIROS_OK) return st;
@@ -1006,6 +1022,7 @@ kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32
     // unconditional relaxation
     const int shape_set[][2] = {{0, 0}, {16, 0}, {0, 2}, {16, 2}, {0, 1}};
     for (int L : lanes_set) {
+        if (L < min_lanes) continue;
         for (int wm : wmax_set) {
             for (const auto &sh : shape_set) {
                 if (L == 1 && sh[1] == 2) continue;  // one lane: the two checked modes coincide
@@ -1029,9 +1046,38 @@ kairos_status kairos_autotune(kairos_graph *g, const kairos_query *sample, int32
             }
         }
     }
+    // the time-ordered mode at 32 and 64 lanes, one or two launches in flight, three block sizes
+    for (int L : {32, 64}) {
+        for (int cc : {1, 2, 4}) {
+            for (int div : {512, 2048, 8192}) {
+                kairos_tuning c = base;
+                c.lanes = L;
+                c.relax_mode = 3;
+                c.concurrent = cc;
+                c.blocks_per_sm = 0;
+                c.block_edges = (int32_t)std::min<int64_t>(std::max<int64_t>(g->m / div, 4096), 1 << 30);
+                g->tuning = c;
+                kairos_status st = kairos_run_queries(g, sample, n, nullptr, nullptr, L);
+                if (st == KAIROS_ERR_OOM) continue;
+                if (st != KAIROS_OK) {
+                    g->tuning = base;
+                    return st;
+                }
+                if (win_ms < 0 || g->last_kernel_ms < win_ms) {
+                    win_ms = g->last_kernel_ms;
+                    win = c;
+                }
+            }
+        }
+    }
     if (win_ms < 0) {
         g->tuning = base;
         return fail(KAIROS_ERR_OOM, "autotune: no launch shape fits in device memory");
+    }
+    if (win.relax_mode == 3) {  // the frontier-mode refinements below do not apply
+        g->tuning = win;
+        if (best) *best = win;
+        return KAIROS_OK;
     }
     // coordinate descent on the winner: chunk size, then resident blocks per SM
     auto try_shape = [&](const kairos_tuning &c) -> kairos_status {

@@ -227,6 +227,8 @@ struct StreamCtr {
     unsigned long long fix_vertices;
     unsigned int fix_rounds;        // fix-up generations run
     unsigned int blocks;            // time blocks swept
+    unsigned int gen_shared;        // fix-up generation after a one-block run of short rounds
+    unsigned int round_shared;      // and its round count within the time block
     // SM cycles summed over warps when StreamArgs::phase_clock is set: 0 block passes,
     // 1 fix-ups, 2 grid barriers, 3 initialisation and read-out
     unsigned long long phase_cycles[4];
@@ -403,7 +405,11 @@ struct kairos_graph {
         unsigned long long *rmask = nullptr;
         int32_t *fq = nullptr;
         size_t bytes = 0;
-    } sw[2];
+    } sw[4];
+    // up to three more streams for time-ordered launches in flight together, with their fork and
+    // join events
+    cudaStream_t sside[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t sfork = nullptr, sjoin[3] = {nullptr, nullptr, nullptr};
     kairos::StreamCtr *sctrs = nullptr, *sctrs_host = nullptr;
     kairos::StreamCtr last_sctr{};  // counters of the last stream-mode launch (diagnostics)
     size_t sctr_slots = 0;

@@ -160,34 +160,119 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t *__restrict_
 
 // Candidate edges of one warp's tile (the records, or a fix-up vertex's edges, that passed
 // both bounds).
+constexpr int ST_CAND = ST_THREADS * ST_KE;  // candidates of one block tile
+
+// Candidate edges (records, or a fix-up vertex's edges, that passed the bounds): the block's
+// pass tile pools them in one list; a fix-up warp uses its own slice of 32 * ST_KE entries.
 struct StreamCand {
-    unsigned long long cm[32 * ST_KE];  // lanes in which the edge may improve its head
-    int32_t u[32 * ST_KE], v[32 * ST_KE];
-    uint32_t t[32 * ST_KE], tau[32 * ST_KE];
+    unsigned long long cm[ST_CAND];  // lanes in which the edge may improve its head
+    int32_t u[ST_CAND], v[ST_CAND];
+    uint32_t t[ST_CAND], tau[ST_CAND];
 };
 
 struct StreamSmem {
     int flag;
+    unsigned bcount[2];      // pooled candidates of the current block tile (by tile parity)
     uint32_t tile[32 * 65];  // readout transpose: 32 vertices x up to 64 lanes (+1 pad)
-    StreamCand cand[ST_THREADS / 32];
+    StreamCand cand;
 };
 
-// Append this thread's flagged edge to the warp's candidate list (ballot prefix); returns the
-// new length.
-__device__ __forceinline__ int cand_push(StreamCand &L, int len, int lane, unsigned long long cm, int32_t u, int32_t v,
-                                         uint32_t t, uint32_t tau) {
+__device__ __forceinline__ void cand_put(StreamCand &L, int pos, unsigned long long cm, int32_t u, int32_t v, uint32_t t,
+                                         uint32_t tau) {
+    L.cm[pos] = cm;
+    L.u[pos] = u;
+    L.v[pos] = v;
+    L.t[pos] = t;
+    L.tau[pos] = tau;
+}
+
+// Append this thread's flagged edge to a warp's slice [off, off + 32 * ST_KE) of the list
+// (ballot prefix); returns the slice's new length.
+__device__ __forceinline__ int cand_push(StreamCand &L, int off, int len, int lane, unsigned long long cm, int32_t u,
+                                         int32_t v, uint32_t t, uint32_t tau) {
     const bool c = cm != 0ull;
     const unsigned m = __ballot_sync(SFULL, c);
-    if (c) {
-        const int pos = len + __popc(m & ((1u << lane) - 1u));
-        L.cm[pos] = cm;
-        L.u[pos] = u;
-        L.v[pos] = v;
-        L.t[pos] = t;
-        L.tau[pos] = tau;
-    }
+    if (c) cand_put(L, off + len + __popc(m & ((1u << lane) - 1u)), cm, u, v, t, tau);
     return len + __popc(m);
 }
+
+// One fix-up vertex u, by one warp: its out-edges departing in [max(its least threshold, tbeg),
+// tend) (binary searches in the time-sorted list), filtered by the reached-lane bounds and
+// relaxed in batches; heads that drop below tend join the queue nq.
+template <int W, typename LamT>
+__device__ __forceinline__ void fix_vertex(const StreamArgs &a, const StreamLaneReg<W> &R, int lane, StreamCand &L,
+                                           int loff, int32_t u, uint32_t tbeg, uint32_t tend, uint32_t twmax,
+                                           int32_t *nq, unsigned *ncount, unsigned long long &fixe) {
+    constexpr int LPT = W / 32;
+    const LamT *__restrict__ lam = (const LamT *)a.lam;
+    if (lane == 0) {
+        atomicAnd(&a.fbm[u >> 5], ~(1u << (u & 31)));
+        __threadfence();  // cleared before the labels are read: a later drop re-queues u
+    }
+    __syncwarp();
+    uint32_t tu[LPT];
+    lane_thresholds<W>(a, R, lane, u, tu);
+    uint32_t tmin = INF;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) tmin = min(tmin, tu[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tmin = min(tmin, __shfl_xor_sync(SFULL, tmin, o));
+    if (tmin >= tend) return;
+    const uint64_t o0 = __ldg(&a.off[u]);
+    const uint32_t deg = (uint32_t)(__ldg(&a.off[u + 1]) - o0);
+    // departures before the block were relaxed in every lane usable then, and a label that
+    // dropped during the block is at least its first departure
+    const uint32_t b0 = warp_lower_bound(a.t + o0, deg, max(tmin, tbeg), lane);
+    const uint32_t b1 = warp_lower_bound(a.t + o0, deg, tend, lane);
+    uint32_t thr[ST_G][LPT];
+#pragma unroll
+    for (int g = 0; g < ST_G; ++g)
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) thr[g][i] = tu[i];
+    // lanes reached at u, from its row (exact when read)
+    unsigned long long lanes_u = 0;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) lanes_u |= (unsigned long long)__ballot_sync(SFULL, tu[i] != INF) << (32 * i);
+    for (uint32_t c0 = b0; c0 < b1; c0 += 32 * ST_KE) {
+        int len = 0;
+#pragma unroll
+        for (int j = 0; j < ST_KE; ++j) {
+            const uint32_t e = c0 + j * 32 + lane;
+            bool ok = e < b1;
+            int32_t d = 0;
+            uint32_t tt = 0, tau = 0;
+            if (ok) {
+                d = __ldg(&a.dst[o0 + e]);
+                tt = __ldg(&a.t[o0 + e]);
+                tau = tt + (uint32_t)__ldg(&lam[o0 + e]);
+                ++fixe;
+                ok = tau <= twmax;
+            }
+            len = cand_push(L, loff, len, lane, ok ? may_improve(a, lanes_u, d, tau) : 0ull, u, d, tt, tau);
+        }
+        __syncwarp();
+        for (int base = 0; base < len; base += ST_G) {
+            const int cnt = min(ST_G, len - base);
+            int32_t v[ST_G];
+            uint32_t t[ST_G], tau[ST_G];
+            unsigned long long cm[ST_G];
+#pragma unroll
+            for (int g = 0; g < ST_G; ++g) {
+                const int k2 = loff + base + (g < cnt ? g : 0);
+                cm[g] = g < cnt ? L.cm[k2] : 0ull;
+                v[g] = L.v[k2];
+                t[g] = L.t[k2];
+                tau[g] = L.tau[k2];
+            }
+            relax_batch<W>(a, R, lane, cnt, thr, v, t, tau, cm, tend, nq, ncount);
+        }
+        __syncwarp();
+    }
+}
+
+// Fix-up frontiers at most this long are finished by one thread block with block barriers
+// (no grid-wide round per step of a short chain).
+constexpr unsigned ST_LOCAL_FIX = 16;
 
 template <int W, typename LamT>
 __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs a) {
@@ -200,7 +285,6 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
     const int64_t n = a.n;
     const size_t nwords = (size_t)((n + 31) >> 5);
     StreamCtr *C = a.ctr;
-    const LamT *__restrict__ lam = (const LamT *)a.lam;
 
     StreamLaneReg<W> R;
     uint32_t twmax = 0;
@@ -222,6 +306,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
         a.rmax[i] = 0u;
     }
     for (size_t i = tid; i < nwords; i += nthr) a.fbm[i] = 0u;
+    if (threadIdx.x == 0) S.bcount[0] = S.bcount[1] = 0;
     if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
     if (blockIdx.x == 0 && threadIdx.x < (unsigned)a.lanes.nlanes) {
         const int q = threadIdx.x;
@@ -234,6 +319,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
 
     unsigned long long scanned = 0, cand = 0, fixe = 0, fixv = 0;
     unsigned gen = 0, fix_rounds = 0;
+    unsigned par = 0;  // parity of the block's pass tiles (selects the pooled candidate count)
     unsigned long long ph[4] = {0, 0, 0, 0};
     long long ph_last = a.phase_clock ? clock64() : 0;
     auto mark = [&](int p) {
@@ -247,16 +333,19 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
     for (int k = a.k_begin; k < a.k_end; ++k) {
         const uint64_t lo = a.bnd[k], hi = a.bnd[k + 1];
         const uint32_t tbeg = a.bt[k], tend = a.bt[k + 1];
-        // ---- pass: every record of the block once, KE per thread, coalesced ----
+        // ---- pass: every record of the block once, coalesced.  A thread block takes ST_CAND
+        // records at a time (KE per thread); the candidates of that tile are pooled and dealt to
+        // its warps in batches, so that a warp whose records hold many does not hold the round.
         {
             int32_t *fq = a.fq[gen & 1];
             unsigned *fcount = &C->fcount[gen % 3].v;
-            for (uint64_t tb = lo + (uint64_t)gw * (32 * ST_KE); tb < hi; tb += (uint64_t)nwarps * (32 * ST_KE)) {
+            const int wib = threadIdx.x >> 5;
+            for (uint64_t tb = lo + (uint64_t)blockIdx.x * ST_CAND; tb < hi; tb += (uint64_t)gridDim.x * ST_CAND, par ^= 1u) {
                 StreamRec r[ST_KE];
                 bool c[ST_KE];
 #pragma unroll
                 for (int j = 0; j < ST_KE; ++j) {
-                    const uint64_t e = tb + (uint64_t)(j * 32 + lane);
+                    const uint64_t e = tb + (uint64_t)(wib * 32 * ST_KE + j * 32 + lane);
                     c[j] = e < hi;
                     if (c[j]) {
                         const int4 x = __ldcs(reinterpret_cast<const int4 *>(a.rec + e));  // read once: streaming
@@ -277,18 +366,24 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                     mn[j] = c[j] ? __ldcg(&a.minrow[r[j].src]) : INF;
                     lu[j] = c[j] ? __ldcg(&a.rmask[r[j].src]) : 0ull;
                 }
-                StreamCand &L = S.cand[threadIdx.x >> 5];
-                int len = 0;
+                unsigned *cntp = &S.bcount[par];
 #pragma unroll
                 for (int j = 0; j < ST_KE; ++j) {
                     const uint32_t tau = r[j].t + r[j].lam;
                     const bool ok = c[j] && r[j].t >= mn[j] && tau <= twmax && lu[j] != 0ull;
-                    len = cand_push(L, len, lane, ok ? may_improve(a, lu[j], r[j].dst, tau) : 0ull, r[j].src, r[j].dst,
-                                    r[j].t, tau);
+                    const unsigned long long cmj = ok ? may_improve(a, lu[j], r[j].dst, tau) : 0ull;
+                    const unsigned m = __ballot_sync(SFULL, cmj != 0ull);
+                    unsigned pos = 0;
+                    if (lane == 0 && m) pos = atomicAdd(cntp, (unsigned)__popc(m));
+                    pos = __shfl_sync(SFULL, pos, 0) + __popc(m & ((1u << lane) - 1u));
+                    if (cmj) cand_put(S.cand, (int)pos, cmj, r[j].src, r[j].dst, r[j].t, tau);
                 }
-                __syncwarp();
-                cand += (lane == 0) ? len : 0;
-                for (int base = 0; base < len; base += ST_G) {
+                __syncthreads();
+                const int len = (int)*cntp;
+                if (threadIdx.x == 0) S.bcount[par ^ 1u] = 0;  // the next tile's count (unused until then)
+                cand += (threadIdx.x == 0) ? len : 0;
+                StreamCand &L = S.cand;
+                for (int base = wib * ST_G; base < len; base += (ST_THREADS / 32) * ST_G) {
                     const int cnt = min(ST_G, len - base);
                     int32_t u[ST_G], v[ST_G];
                     uint32_t t[ST_G], tau[ST_G], thr[ST_G][LPT];
@@ -317,7 +412,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                         }
                     relax_batch<W>(a, R, lane, cnt, thr, v, t, tau, cm, tend, fq, fcount);
                 }
-                __syncwarp();
+                __syncthreads();  // the list is rewritten by the next tile
             }
         }
         mark(0);
@@ -331,81 +426,48 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                 if (tid == 0) atomicCAS(&C->err, 0, KERR_FIX_ROUNDS);
                 return;
             }
-            if (tid == 0) {
-                C->fcount[(gen + 2) % 3].v = 0;
+            const int loff = (threadIdx.x >> 5) * 32 * ST_KE;  // this warp's slice of the list
+            if (F <= ST_LOCAL_FIX) {
+                // a short frontier: block 0 runs the rounds alone, with block barriers, while it
+                // stays short; the others wait at the grid barrier
+                if (blockIdx.x == 0) {
+                    unsigned g2 = gen, f = F, rr = round;
+                    while (f != 0 && f <= ST_LOCAL_FIX && rr < a.max_fix_rounds) {
+                        if (threadIdx.x == 0) C->fcount[(g2 + 2) % 3].v = 0;
+                        const int32_t *cq = a.fq[g2 & 1];
+                        for (unsigned idx = threadIdx.x >> 5; idx < f; idx += ST_THREADS / 32) {
+                            ++fixv;
+                            fix_vertex<W, LamT>(a, R, lane, S.cand, loff, __ldcg(&cq[idx]), tbeg, tend, twmax,
+                                                a.fq[(g2 + 1) & 1], &C->fcount[(g2 + 1) % 3].v, fixe);
+                        }
+                        __threadfence();
+                        __syncthreads();
+                        ++g2;
+                        ++rr;
+                        if (threadIdx.x == 0) ++fix_rounds;
+                        f = __ldcg(&C->fcount[g2 % 3].v);
+                        __syncthreads();  // every thread has read f before the next reset
+                    }
+                    if (threadIdx.x == 0) {
+                        C->gen_shared = g2;
+                        C->round_shared = rr;
+                    }
+                }
+                mark(1);
+                if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
+                mark(2);
+                gen = __ldcg(&C->gen_shared);
+                round = __ldcg(&C->round_shared) - 1;  // the loop adds one
+                continue;
             }
+            if (tid == 0) C->fcount[(gen + 2) % 3].v = 0;
             ++fix_rounds;
             const int32_t *cq = a.fq[gen & 1];
             int32_t *nq = a.fq[(gen + 1) & 1];
             unsigned *ncount = &C->fcount[(gen + 1) % 3].v;
-            StreamCand &L = S.cand[threadIdx.x >> 5];
             for (unsigned idx = gw; idx < F; idx += nwarps) {  // queue entries dealt to warps in turn
-                const int32_t u = __ldcg(&cq[idx]);
-                if (lane == 0) {
-                    atomicAnd(&a.fbm[u >> 5], ~(1u << (u & 31)));
-                    __threadfence();  // cleared before the labels are read: a later drop re-queues u
-                }
-                __syncwarp();
                 ++fixv;
-                uint32_t tu[LPT];
-                lane_thresholds<W>(a, R, lane, u, tu);
-                uint32_t tmin = INF;
-#pragma unroll
-                for (int i = 0; i < LPT; ++i) tmin = min(tmin, tu[i]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) tmin = min(tmin, __shfl_xor_sync(SFULL, tmin, o));
-                if (tmin >= tend) continue;
-                const uint64_t o0 = __ldg(&a.off[u]);
-                const uint32_t deg = (uint32_t)(__ldg(&a.off[u + 1]) - o0);
-                // departures before the block were relaxed in every lane usable then, and a
-                // label that dropped during the block is at least its first departure
-                const uint32_t b0 = warp_lower_bound(a.t + o0, deg, max(tmin, tbeg), lane);
-                const uint32_t b1 = warp_lower_bound(a.t + o0, deg, tend, lane);
-                uint32_t thr[ST_G][LPT];
-#pragma unroll
-                for (int g = 0; g < ST_G; ++g)
-#pragma unroll
-                    for (int i = 0; i < LPT; ++i) thr[g][i] = tu[i];
-                // lanes reached at u, from its row (exact when read)
-                unsigned long long lanes_u = 0;
-#pragma unroll
-                for (int i = 0; i < LPT; ++i)
-                    lanes_u |= (unsigned long long)__ballot_sync(SFULL, tu[i] != INF) << (32 * i);
-                for (uint32_t c0 = b0; c0 < b1; c0 += 32 * ST_KE) {
-                    int len = 0;
-#pragma unroll
-                    for (int j = 0; j < ST_KE; ++j) {
-                        const uint32_t e = c0 + j * 32 + lane;
-                        bool ok = e < b1;
-                        int32_t d = 0;
-                        uint32_t tt = 0, tau = 0;
-                        if (ok) {
-                            d = __ldg(&a.dst[o0 + e]);
-                            tt = __ldg(&a.t[o0 + e]);
-                            tau = tt + (uint32_t)__ldg(&lam[o0 + e]);
-                            ++fixe;
-                            ok = tau <= twmax;
-                        }
-                        len = cand_push(L, len, lane, ok ? may_improve(a, lanes_u, d, tau) : 0ull, u, d, tt, tau);
-                    }
-                    __syncwarp();
-                    for (int base = 0; base < len; base += ST_G) {
-                        const int cnt = min(ST_G, len - base);
-                        int32_t v[ST_G];
-                        uint32_t t[ST_G], tau[ST_G];
-                        unsigned long long cm[ST_G];
-#pragma unroll
-                        for (int g = 0; g < ST_G; ++g) {
-                            const int k2 = base + (g < cnt ? g : 0);
-                            cm[g] = g < cnt ? L.cm[k2] : 0ull;
-                            v[g] = L.v[k2];
-                            t[g] = L.t[k2];
-                            tau[g] = L.tau[k2];
-                        }
-                        relax_batch<W>(a, R, lane, cnt, thr, v, t, tau, cm, tend, nq, ncount);
-                    }
-                    __syncwarp();
-                }
+                fix_vertex<W, LamT>(a, R, lane, S.cand, loff, __ldcg(&cq[idx]), tbeg, tend, twmax, nq, ncount, fixe);
             }
             mark(1);
             if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
@@ -459,7 +521,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
         atomicAdd(&C->fix_vertices, fixv);
     }
     if (tid == 0) {
-        C->fix_rounds = fix_rounds;
+        C->fix_rounds = fix_rounds;  // thread 0 counts the grid-wide and the one-block rounds
         C->blocks = (unsigned)(a.k_end - a.k_begin);
     }
     mark(3);

@@ -24,7 +24,7 @@ class FakeGraph(kx.Graph):
 def fake_library(monkeypatch):
     calls = {"autotune": 0, "set": []}
 
-    def autotune(handle, sample):
+    def autotune(handle, sample, min_lanes=1):
         calls["autotune"] += 1
         t = kx.kairos_tuning()
         t.lanes, t.warp_max_edges, t.chunk_edges, t.concurrent = 16, 512, 1024, 2

@@ -78,11 +78,12 @@ def test_stream_mode_matches_oracle(tiny, lanes, on_device, block_edges):
 
 
 @pytest.mark.parametrize("lanes", [32, 64])
-def test_stream_mode_two_launches_in_flight_and_replay(tiny, lanes):
-    """Launches alternate between two streams and workspaces; the call repeats as a
+@pytest.mark.parametrize("concurrent", [2, 4])
+def test_stream_mode_launches_in_flight_and_replay(tiny, lanes, concurrent):
+    """Launches are dealt to two or four streams and workspaces; the call repeats as a
     captured CUDA graph with identical labels."""
     el, orc, g = tiny
-    g.set_tuning(lanes=lanes, relax_mode=3, concurrent=2, block_edges=2000)
+    g.set_tuning(lanes=lanes, relax_mode=3, concurrent=concurrent, block_edges=2000)
     qs = mixed_queries(el, 3 * lanes + 5, 0xB200)
     before = g.info().graph_launches
     first, stats = run(g, el.n, qs)
@@ -159,6 +160,8 @@ def test_stream_mode_edge_cases():
         g.set_tuning(lanes=16, relax_mode=3)
     with pytest.raises(kx.KairosError):
         g.set_tuning(lanes=64, relax_mode=0)
+    with pytest.raises(kx.KairosError):
+        g.set_tuning(lanes=16, relax_mode=0, concurrent=4)
     g.close()
 
 
