@@ -375,9 +375,12 @@ kairos_status ensure_sctr_slots(kairos_graph *g, size_t count) {
     return KAIROS_OK;
 }
 
-kairos_status stream_error(int err) {
-    if (err == KERR_FIX_ROUNDS) return fail(KAIROS_ERR_TIMEOUT, "stream edge-map: fix-up round cap reached");
-    if (err == KERR_BARRIER_TIMEOUT) return fail(KAIROS_ERR_TIMEOUT, "stream edge-map: a grid barrier wait ran past its limit");
+kairos_status stream_error(const StreamCtr &c) {
+    const std::string at = " (time block " + std::to_string(c.err_block) + ", fix-up round " +
+                           (c.err_round == 0xFFFFFFFFu ? std::string("-") : std::to_string(c.err_round)) + ")";
+    if (c.err == KERR_FIX_ROUNDS) return fail(KAIROS_ERR_TIMEOUT, "stream edge-map: fix-up round cap reached");
+    if (c.err == KERR_BARRIER_TIMEOUT)
+        return fail(KAIROS_ERR_TIMEOUT, "stream edge-map: a grid barrier wait ran past its limit" + at);
     return fail(KAIROS_ERR_INTERNAL, "stream edge-map: device error");
 }
 
@@ -587,7 +590,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
     g->last_sctr = g->sctrs_host[plan.size() - 1];
     for (size_t i = 0; i < plan.size(); ++i) {
         const StreamCtr &res = g->sctrs_host[i];
-        if (res.err) return stream_error(res.err);
+        if (res.err) return stream_error(res);
         if (stats) {
             for (size_t j = 0; j < plan[i].qid.size(); ++j) {
                 kairos_query_stats &S = stats[plan[i].qid[j]];
@@ -1186,13 +1189,14 @@ int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uin
     return r;
 }
 
-int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out10) {
-    if (!g || !out10) return 0;
+int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out15) {
+    if (!g || !out15) return 0;
     const StreamCtr &c = g->last_sctr;
-    const uint64_t v[10] = {c.blocks, c.fix_rounds, c.fix_vertices, c.fix_edges, c.cand, c.scanned,
-                            c.phase_cycles[0], c.phase_cycles[1], c.phase_cycles[2], c.phase_cycles[3]};
-    for (int i = 0; i < 10; ++i) out10[i] = v[i];
-    return 10;
+    const uint64_t v[15] = {c.blocks, c.fix_rounds, c.fix_vertices, c.fix_edges, c.cand, c.scanned,
+                            c.phase_cycles[0], c.phase_cycles[1], c.phase_cycles[2], c.phase_cycles[3],
+                            c.cand_lanes[0], c.cand_lanes[1], c.cand_lanes[2], c.cand_lanes[3], c.cand_pairs};
+    for (int i = 0; i < 15; ++i) out15[i] = v[i];
+    return 15;
 }
 
 int32_t kairos_last_phase_cycles(const kairos_graph *g, uint64_t *cycles8) {

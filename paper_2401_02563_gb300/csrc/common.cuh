@@ -227,8 +227,13 @@ struct StreamCtr {
     unsigned long long fix_vertices;
     unsigned int fix_rounds;        // fix-up generations run
     unsigned int blocks;            // time blocks swept
+    unsigned int err_block, err_round;  // where the launch stopped on an error (time block, round)
     unsigned int gen_shared;        // fix-up generation after a one-block run of short rounds
     unsigned int round_shared;      // and its round count within the time block
+    // diagnostics (phase_clock): pass candidates by number of candidate lanes (1, 2-4, 5-16,
+    // 17-64), and candidate lanes in all
+    unsigned long long cand_lanes[4];
+    unsigned long long cand_pairs;
     // SM cycles summed over warps when StreamArgs::phase_clock is set: 0 block passes,
     // 1 fix-ups, 2 grid barriers, 3 initialisation and read-out
     unsigned long long phase_cycles[4];

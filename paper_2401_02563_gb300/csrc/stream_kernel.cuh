@@ -270,9 +270,11 @@ __device__ __forceinline__ void fix_vertex(const StreamArgs &a, const StreamLane
     }
 }
 
-// Fix-up frontiers at most this long are finished by one thread block with block barriers
-// (no grid-wide round per step of a short chain).
+// Fix-up frontiers at most this long are advanced by one thread block with block barriers (no
+// grid-wide round per step of a short chain), for at most ST_LOCAL_ROUNDS rounds at a time so
+// that the other blocks' wait at the grid barrier stays short.
 constexpr unsigned ST_LOCAL_FIX = 16;
+constexpr unsigned ST_LOCAL_ROUNDS = 64;
 
 template <int W, typename LamT>
 __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs a) {
@@ -372,6 +374,11 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                     const uint32_t tau = r[j].t + r[j].lam;
                     const bool ok = c[j] && r[j].t >= mn[j] && tau <= twmax && lu[j] != 0ull;
                     const unsigned long long cmj = ok ? may_improve(a, lu[j], r[j].dst, tau) : 0ull;
+                    if (a.phase_clock && cmj) {  // diagnostics: how many lanes a candidate carries
+                        const int pc = __popcll(cmj);
+                        atomicAdd(&C->cand_lanes[pc == 1 ? 0 : pc <= 4 ? 1 : pc <= 16 ? 2 : 3], 1ull);
+                        atomicAdd(&C->cand_pairs, (unsigned long long)pc);
+                    }
                     const unsigned m = __ballot_sync(SFULL, cmj != 0ull);
                     unsigned pos = 0;
                     if (lane == 0 && m) pos = atomicAdd(cntp, (unsigned)__popc(m));
@@ -416,7 +423,13 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
             }
         }
         mark(0);
-        if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
+        if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) {
+            if (tid == 0) {
+                C->err_block = (unsigned)k;
+                C->err_round = 0xFFFFFFFFu;  // after the block's pass
+            }
+            return;
+        }
         mark(2);
         // ---- fix-ups: frontier rounds over the block's departures ----
         for (unsigned round = 0;; ++round) {
@@ -432,7 +445,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                 // stays short; the others wait at the grid barrier
                 if (blockIdx.x == 0) {
                     unsigned g2 = gen, f = F, rr = round;
-                    while (f != 0 && f <= ST_LOCAL_FIX && rr < a.max_fix_rounds) {
+                    while (f != 0 && f <= ST_LOCAL_FIX && rr < a.max_fix_rounds && rr - round < ST_LOCAL_ROUNDS) {
                         if (threadIdx.x == 0) C->fcount[(g2 + 2) % 3].v = 0;
                         const int32_t *cq = a.fq[g2 & 1];
                         for (unsigned idx = threadIdx.x >> 5; idx < f; idx += ST_THREADS / 32) {
@@ -454,7 +467,13 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                     }
                 }
                 mark(1);
-                if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
+                if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) {
+                    if (tid == 0) {
+                        C->err_block = (unsigned)k;
+                        C->err_round = round;
+                    }
+                    return;
+                }
                 mark(2);
                 gen = __ldcg(&C->gen_shared);
                 round = __ldcg(&C->round_shared) - 1;  // the loop adds one
@@ -470,7 +489,13 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                 fix_vertex<W, LamT>(a, R, lane, S.cand, loff, __ldcg(&cq[idx]), tbeg, tend, twmax, nq, ncount, fixe);
             }
             mark(1);
-            if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
+            if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) {
+                if (tid == 0) {
+                    C->err_block = (unsigned)k;
+                    C->err_round = round;
+                }
+                return;
+            }
             mark(2);
             ++gen;
         }
