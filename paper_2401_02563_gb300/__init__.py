@@ -573,14 +573,15 @@ def kairos_last_phase_cycles(g):
 
 
 STREAM_COUNTERS = ("blocks", "fix_rounds", "fix_vertices", "fix_edges", "candidates", "scanned",
-                   "pass_cycles", "fixup_cycles", "barrier_cycles", "init_readout_cycles",
-                   "cand_1_lane", "cand_2_4_lanes", "cand_5_16_lanes", "cand_17_64_lanes", "cand_lanes")
+                   "pass_filter_cycles", "fixup_cycles", "barrier_init_readout_cycles", "pass_relax_cycles",
+                   "cand_1_lane", "cand_2_4_lanes", "cand_5_16_lanes", "cand_17_64_lanes", "cand_lanes",
+                   "cand_improving", "lanes_lowered")
 
 
 def kairos_last_stream_profile(g):
     """Counters of the last time-ordered (relax_mode 3) launch (cycles and lane counts need
     KAIROS_PHASE_CLOCK=1)."""
-    c = np.zeros(15, np.uint64)
+    c = np.zeros(len(STREAM_COUNTERS), np.uint64)
     lib().kairos_last_stream_profile(g, c.ctypes.data)
     return dict(zip(STREAM_COUNTERS, c.tolist()))
 

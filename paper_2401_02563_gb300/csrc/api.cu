@@ -59,27 +59,23 @@ void Allocator::put(void *p) const {
 
 namespace {
 
-bool device_ptr(const void *p) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 // Where the kernels may write an output buffer directly: device memory as it is, and
 // page-locked host memory through its device mapping (the writes cross the CPU-GPU link
-// inside the launch, no staging copy).  Pageable host memory returns nullptr: it is staged
-// on the device and copied.
-uint32_t *direct_out(uint32_t *p) {
+// inside the launch, no staging copy).  Pageable host memory gives nullptr: it is staged
+// on the device and copied.  *pinned tells page-locked host memory apart (its device mapping
+// may be the same address, as on systems whose GPU shares the host's page tables).
+uint32_t *direct_out(uint32_t *p, bool *pinned) {
+    *pinned = false;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
     if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
-    if (at.type == cudaMemoryTypeHost && at.devicePointer) return (uint32_t *)at.devicePointer;
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        *pinned = true;
+        return (uint32_t *)at.devicePointer;
+    }
     return nullptr;
 }
 
@@ -295,10 +291,10 @@ void release_stream_work(kairos_graph *g) {
     for (auto &sw : g->sw) {
         g->A.put(sw.arr);
         g->A.put(sw.minrow);
-        g->A.put(sw.rmax);
-        g->A.put(sw.rmask);
+        g->A.put(sw.rsum);
         g->A.put(sw.fbm);
         g->A.put(sw.fq);
+        g->A.put(sw.stage);
         sw = kairos_graph::StreamWork();
     }
 }
@@ -339,23 +335,34 @@ kairos_status ensure_stream_work(kairos_graph *g, int W, int slots) {
         if (sw.arr && sw.lanes == W) continue;
         g->A.put(sw.arr);
         g->A.put(sw.minrow);
-        g->A.put(sw.rmax);
-        g->A.put(sw.rmask);
+        g->A.put(sw.rsum);
         g->A.put(sw.fbm);
         g->A.put(sw.fq);
+        g->A.put(sw.stage);
         sw = kairos_graph::StreamWork();
         sw.arr = (uint32_t *)g->A.get((size_t)n * W * 4);
         sw.minrow = (uint32_t *)g->A.get((size_t)n * 4);
-        sw.rmax = (uint32_t *)g->A.get((size_t)n * 4);
-        sw.rmask = (unsigned long long *)g->A.get((size_t)n * 8);
+        sw.rsum = (unsigned long long *)g->A.get((size_t)n * 16);
         sw.fbm = (uint32_t *)g->A.get((size_t)nwords * 4);
         sw.fq = (int32_t *)g->A.get((size_t)n * 2 * 4);
-        if (!sw.arr || !sw.minrow || !sw.rmax || !sw.rmask || !sw.fbm || !sw.fq) {
+        if (!sw.arr || !sw.minrow || !sw.rsum || !sw.fbm || !sw.fq) {
             release_stream_work(g);
             return fail(KAIROS_ERR_OOM, "stream workspace: device allocation failed");
         }
         sw.lanes = W;
-        sw.bytes = (size_t)n * W * 4 + (size_t)n * 24 + (size_t)nwords * 4;
+        sw.bytes = (size_t)n * W * 4 + (size_t)n * 28 + (size_t)nwords * 4;
+    }
+    return KAIROS_OK;
+}
+
+// Device staging rows for host outputs of the first `slots` launch slots.
+kairos_status ensure_stream_stage(kairos_graph *g, int slots) {
+    for (int i = 0; i < slots; ++i) {
+        auto &sw = g->sw[i];
+        if (sw.stage) continue;
+        sw.stage = (uint32_t *)g->A.get((size_t)g->n * sw.lanes * 4);
+        if (!sw.stage) return fail(KAIROS_ERR_OOM, "stream staging: device allocation failed");
+        sw.bytes += (size_t)g->n * sw.lanes * 4;
     }
     return KAIROS_OK;
 }
@@ -396,11 +403,12 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
                                  kairos_query_stats *stats, int lanes) {
     const int64_t n = g->n;
     uint32_t *const host_out = out;  // the caller's pointer (staged copies go there)
+    bool dev = true, pinned = false;  // outputs the kernels can write (device or page-locked memory)
     if (out) {
-        uint32_t *d = direct_out(out);
+        uint32_t *d = direct_out(out, &pinned);
+        dev = d != nullptr;
         if (d) out = d;
     }
-    const bool dev = out ? out != host_out || device_ptr(out) : true;
     bool need_f = false, need_r = false;
     int64_t n_launch = 0;
     for (int kind = 0; kind < 2; ++kind) {
@@ -411,23 +419,21 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
     }
     const int C = dev ? (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)std::max(g->tuning.concurrent, 1), n_launch, 4}))
                       : 1;
+    // Host outputs are staged: each launch writes its rows to device memory and the copy engine
+    // moves them to the host on the launch's stream, overlapping the launches still running.
+    // Only a page-locked output of a call with one launch in flight is written by the kernel
+    // directly (kernel writes across the CPU-GPU link stalled the grid barriers of a launch
+    // running beside them).
+    const bool staged = out && (!dev || (pinned && C >= 2));
     kairos_status st = ensure_time_stream(g, need_f, need_r);
     if (st != KAIROS_OK) return st;
     st = ensure_stream_work(g, lanes, C);
     if (st != KAIROS_OK) return st;
-    auto &w = g->work;
-    if (out && !dev && !w.stage) {
-        // host outputs: rows are staged on the device and copied after each launch
-        w.stage = (uint32_t *)g->A.get((size_t)n * lanes * 4);
-        if (!w.stage) return fail(KAIROS_ERR_OOM, "stream staging: device allocation failed");
-        w.bytes += (size_t)n * lanes * 4;
-    } else if (out && !dev && w.stage && w.lanes < lanes) {
-        g->A.put(w.stage);
-        w.bytes -= (size_t)n * std::max(w.lanes, 1) * 4;
-        w.stage = (uint32_t *)g->A.get((size_t)n * lanes * 4);
-        if (!w.stage) return fail(KAIROS_ERR_OOM, "stream staging: device allocation failed");
-        w.bytes += (size_t)n * lanes * 4;
+    if (staged) {
+        st = ensure_stream_stage(g, C);
+        if (st != KAIROS_OK) return st;
     }
+    auto &w = g->work;
     if (C >= 2 && !g->sfork)
         KAIROS_CUDA(cudaEventCreateWithFlags(&g->sfork, cudaEventDisableTiming), "concurrent launches: event");
     for (int k = 0; k + 1 < C; ++k)
@@ -468,7 +474,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
                     a.lanes.mirror_mask |= 1ull << j;
                 }
                 if (Q.strict) a.lanes.strict_mask |= 1ull << j;
-                a.lanes.row[j] = (out && dev) ? idx[c + j] : j;
+                a.lanes.row[j] = (out && !staged) ? idx[c + j] : j;
                 lo_t = std::min(lo_t, a.lanes.ta[j]);
                 hi_t = std::max(hi_t, a.lanes.tw[j]);
             }
@@ -493,12 +499,11 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
             const auto &sw = g->sw[slot];
             a.arr = sw.arr;
             a.minrow = sw.minrow;
-            a.rmax = sw.rmax;
-            a.rmask = sw.rmask;
+            a.rsum = sw.rsum;
             a.fbm = sw.fbm;
             a.fq[0] = sw.fq;
             a.fq[1] = sw.fq + n;
-            a.out = out ? (dev ? out : w.stage) : nullptr;
+            a.out = out ? (staged ? sw.stage : out) : nullptr;
             a.out_stride = n;
             a.max_fix_rounds = round_cap;
             a.spin_limit = spin;
@@ -506,7 +511,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
             static const int phase_clock = getenv("KAIROS_PHASE_CLOCK") ? atoi(getenv("KAIROS_PHASE_CLOCK")) : 0;
             a.phase_clock = phase_clock;
             P.qid.assign(idx.begin() + c, idx.begin() + c + k);
-            P.host_out = out && !dev;
+            P.host_out = staged;
             plan.push_back(std::move(P));
         }
     }
@@ -531,11 +536,12 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
             cudaStream_t si = slot ? g->sside[slot - 1] : s;
             KAIROS_CUDA(cudaMemsetAsync(plan[i].a.ctr, 0, sizeof(StreamCtr), si), "stream edge-map counters");
             KAIROS_CUDA(stream_launch(plan[i].a, lanes, g->lam_bits, grid, si), "stream edge-map launch");
-            if (direct && plan[i].host_out) {
+            if (direct && plan[i].host_out) {  // the copy engine, on the launch's stream
                 const std::vector<int> &q = plan[i].qid;
+                const uint32_t *src = g->sw[slot].stage;
                 for (size_t j = 0; j < q.size(); ++j)
-                    KAIROS_CUDA(cudaMemcpyAsync(host_out + (int64_t)q[j] * n, w.stage + (int64_t)j * n, (size_t)n * 4,
-                                                cudaMemcpyDeviceToHost, s),
+                    KAIROS_CUDA(cudaMemcpyAsync(host_out + (int64_t)q[j] * n, src + (int64_t)j * n, (size_t)n * 4,
+                                                cudaMemcpyDeviceToHost, si),
                                 "copy labels to host");
             }
         }
@@ -547,7 +553,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
     };
 
     KAIROS_CUDA(cudaEventRecord(w.ev0, s), "event record");
-    const bool capturable = dev && s != nullptr && !getenv("KAIROS_NO_GRAPH");
+    const bool capturable = dev && !staged && s != nullptr && !getenv("KAIROS_NO_GRAPH");
     bool launched = false;
     if (capturable) {
         std::string key("stream", 6);
@@ -617,23 +623,24 @@ kairos_status kairos::kairos_run_queries(kairos_graph *g, const kairos_query *qs
     lanes = std::min(lanes, MAX_LANES);
     const int64_t n = g->n;
     uint32_t *const host_out = out;  // the caller's pointer (staged copies go there)
-    if (out) {
-        uint32_t *d = direct_out(out);
-        if (d) out = d;
-    }
     // page-locked host outputs are written directly, like device ones, but never serve as
     // the one-lane label array (its atomics would cross the CPU-GPU link)
-    const bool pinned = out && out != host_out;
-    const bool dev = out ? pinned || device_ptr(out) : true;
+    bool pinned = false, dev = true;
+    if (out) {
+        uint32_t *d = direct_out(out, &pinned);
+        dev = d != nullptr;
+        if (d) out = d;
+    }
     // launches kept in flight together: two (second workspace and stream) when asked for, the
-    // outputs are device memory and the call has at least two launches
+    // outputs are device memory and the call has at least two launches (kernel writes to
+    // page-locked host memory stalled the grid barriers of a launch running beside them)
     int64_t n_launch = 0;
     for (int kind = 0; kind < 2; ++kind) {
         int64_t c = 0;
         for (int i = 0; i < nq; ++i) c += qs[i].kind == kind;
         n_launch += (c + lanes - 1) / lanes;
     }
-    const int C = (dev && g->tuning.concurrent >= 2 && n_launch >= 2) ? 2 : 1;
+    const int C = (dev && !pinned && g->tuning.concurrent >= 2 && n_launch >= 2) ? 2 : 1;
     kairos_status st = ensure_work(g, lanes, out && !dev && lanes > 1, C == 2);
     if (st != KAIROS_OK) return st;
     auto &w = g->work;
@@ -1189,14 +1196,15 @@ int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uin
     return r;
 }
 
-int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out15) {
-    if (!g || !out15) return 0;
+int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out17) {
+    if (!g || !out17) return 0;
     const StreamCtr &c = g->last_sctr;
-    const uint64_t v[15] = {c.blocks, c.fix_rounds, c.fix_vertices, c.fix_edges, c.cand, c.scanned,
+    const uint64_t v[17] = {c.blocks, c.fix_rounds, c.fix_vertices, c.fix_edges, c.cand, c.scanned,
                             c.phase_cycles[0], c.phase_cycles[1], c.phase_cycles[2], c.phase_cycles[3],
-                            c.cand_lanes[0], c.cand_lanes[1], c.cand_lanes[2], c.cand_lanes[3], c.cand_pairs};
-    for (int i = 0; i < 15; ++i) out15[i] = v[i];
-    return 15;
+                            c.cand_lanes[0], c.cand_lanes[1], c.cand_lanes[2], c.cand_lanes[3], c.cand_pairs,
+                            c.cand_improving, c.lanes_lowered};
+    for (int i = 0; i < 17; ++i) out17[i] = v[i];
+    return 17;
 }
 
 int32_t kairos_last_phase_cycles(const kairos_graph *g, uint64_t *cycles8) {

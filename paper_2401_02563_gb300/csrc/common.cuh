@@ -221,6 +221,7 @@ struct StreamCtr {
     unsigned int pad0[29];
     PaddedU32 fcount[3];  // fix-up queue lengths, by generation mod 3
     PaddedU32 fnext[3];   // fix-up vertices claimed, by generation mod 3
+    PaddedU32 claim[2];   // pass tiles claimed past the first gridDim.x, by time block parity
     unsigned long long scanned;     // stream records read plus fix-up edges read
     unsigned long long cand;        // records whose lanes were examined
     unsigned long long fix_edges;   // edges read by fix-ups
@@ -228,14 +229,21 @@ struct StreamCtr {
     unsigned int fix_rounds;        // fix-up generations run
     unsigned int blocks;            // time blocks swept
     unsigned int err_block, err_round;  // where the launch stopped on an error (time block, round)
-    unsigned int gen_shared;        // fix-up generation after a one-block run of short rounds
-    unsigned int round_shared;      // and its round count within the time block
+    // fix-up generation and round count within the time block after a one-block run of short
+    // rounds, by run parity: a block may still read run e's pair while block 0 writes run e + 1's
+    unsigned int gen_shared[2];
+    unsigned int round_shared[2];
+    unsigned long long fread;       // frontier-length reads done, one per block and round: a
+                                    // one-block run reuses the read slot only after all of them
     // diagnostics (phase_clock): pass candidates by number of candidate lanes (1, 2-4, 5-16,
     // 17-64), and candidate lanes in all
     unsigned long long cand_lanes[4];
     unsigned long long cand_pairs;
-    // SM cycles summed over warps when StreamArgs::phase_clock is set: 0 block passes,
-    // 1 fix-ups, 2 grid barriers, 3 initialisation and read-out
+    unsigned long long cand_improving;  // candidates (pass and fix-ups) that lowered some label
+    unsigned long long lanes_lowered;   // labels lowered
+    // SM cycles summed over warps when StreamArgs::phase_clock is set: 0 block passes (reading
+    // and filtering records), 1 fix-ups, 2 grid barriers, initialisation and read-out, 3 the
+    // passes' candidate relaxations
     unsigned long long phase_cycles[4];
     unsigned long long relaxed[STREAM_MAX_LANES];
     unsigned int reached[STREAM_MAX_LANES];
@@ -254,9 +262,9 @@ struct StreamArgs {
     int64_t n;
     uint32_t *arr;     // [n][W] labels
     uint32_t *minrow;  // [n] at most the least label of the vertex over the lanes
-    unsigned long long *rmask;  // [n] lanes in which the vertex has a finite label (may lag, never ahead)
-    uint32_t *rmax;    // [n] at least every label of the vertex in a lane of rmask (raised before a
-                       // lane joins rmask, so a reader that sees the lane sees the bound)
+    unsigned long long *rsum;  // [n][2] per half of 32 lanes: (bound << 32) | lanes of the half in
+                               // which the vertex has a finite label (may lag, never ahead); the
+                               // bound >= every label of the vertex in those lanes
     uint32_t *fbm;     // fix-up dedupe bitmap, ceil(n/32) words (all clear between blocks)
     int32_t *fq[2];    // fix-up queues, n entries each
     StreamCtr *ctr;
@@ -406,9 +414,10 @@ struct kairos_graph {
     kairos::TimeStream ts_fwd, ts_rev;
     struct StreamWork {
         int lanes = 0;
-        uint32_t *arr = nullptr, *minrow = nullptr, *rmax = nullptr, *fbm = nullptr;
-        unsigned long long *rmask = nullptr;
+        uint32_t *arr = nullptr, *minrow = nullptr, *fbm = nullptr;
+        unsigned long long *rsum = nullptr;
         int32_t *fq = nullptr;
+        uint32_t *stage = nullptr;  // [W][n] labels bound for host memory (copied by the copy engine)
         size_t bytes = 0;
     } sw[4];
     // up to three more streams for time-ordered launches in flight together, with their fork and

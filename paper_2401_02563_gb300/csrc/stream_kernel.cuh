@@ -10,9 +10,10 @@
 //            at the lane's source) and t + lam <= tw_q: arr[v][q] = min(arr[v][q], t + lam)
 //            (Alg. 2's Update).  Per-vertex summaries skip most records without touching the
 //            W-lane label rows: minrow[u] <= every label of u (a record with t < minrow[u] is
-//            usable in no lane), rmask[.] the lanes in which a vertex is reached, and rmax[v]
-//            >= every label of v in those lanes.  A record can only improve v in a lane where
-//            u is reached and either v is not (yet) or t + lam < rmax[v].
+//            usable in no lane), and per half of 32 lanes one word rsum[.][h] holding the lanes
+//            of the half in which the vertex is reached and a bound >= every label of the
+//            vertex in those lanes.  A record can only improve v in a lane where u is reached
+//            and either v is not (yet) or t + lam is below the bound of v's half.
 //   fix-ups: a label that drops to a time x < T_{k+1} during the block may make records of
 //            the same block usable after the pass already read them.  Such vertices form a
 //            frontier; each round relaxes their out-edges departing in [x, T_{k+1}) (a binary
@@ -60,33 +61,87 @@ __device__ __forceinline__ void lane_thresholds(const StreamArgs &a, const Strea
 
 constexpr int ST_G = 4;  // candidate edges a warp has in flight together
 
+// Diagnostic counts of the thread block (with StreamArgs::phase_clock): candidates by lane count
+// (1, 2-4, 5-16, 17-64), candidate lanes, improving candidates, labels lowered; added to the
+// launch's counters at its end.  Shared-memory atomics keep the counting cheap.
+__device__ __forceinline__ unsigned long long *diag_counts() {
+    __shared__ unsigned long long d[8];
+    return d;
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
+// Reached-lane summary of one vertex: per half h of 32 lanes the word rsum[2 v + h] = (bound <<
+// 32) | lanes of the half in which the vertex has a finite label, the bound >= each of those
+// labels.  A word changes as a whole (compare-and-swap), so every plain 64-bit read of it is a
+// consistent (lanes, bound) pair.
+template <int W>
+__device__ __forceinline__ unsigned long long reached_lanes(const StreamArgs &a, int32_t u) {
+    if (W == 32) return (uint32_t)__ldcg(&a.rsum[2 * (size_t)u]);
+    const ulonglong2 s = __ldcg(reinterpret_cast<const ulonglong2 *>(a.rsum) + u);
+    return (uint32_t)s.x | ((unsigned long long)(uint32_t)s.y << 32);
+}
+
 // The lanes of `lanes_u` (lanes where the tail is reached) in which an edge into v arriving at
-// tau can improve v: those not yet reached at v, plus, when the arrival is below rmax[v], those
-// reached there.  rmask[v] is read with acquire so that rmax[v] covers every lane it shows.
+// tau can improve v: those not yet reached at v, plus, in a half whose bound is above tau, the
+// ones reached there.
+template <int W>
 __device__ __forceinline__ unsigned long long may_improve(const StreamArgs &a, unsigned long long lanes_u, int32_t v,
                                                           uint32_t tau) {
-    const unsigned long long lv = ld_acquire64(&a.rmask[v]);
-    const unsigned long long fresh = lanes_u & ~lv, known = lanes_u & lv;
-    return fresh | ((known && tau < __ldcg(&a.rmax[v])) ? known : 0ull);
+    unsigned long long w[2];
+    if (W == 32) {
+        w[0] = __ldcg(&a.rsum[2 * (size_t)v]);
+        w[1] = 0ull;
+    } else {
+        const ulonglong2 s = __ldcg(reinterpret_cast<const ulonglong2 *>(a.rsum) + v);
+        w[0] = s.x;
+        w[1] = s.y;
+    }
+    unsigned long long cm = 0ull;
+#pragma unroll
+    for (int h = 0; h < W / 32; ++h) {
+        const uint32_t lu = (uint32_t)(lanes_u >> (32 * h)), lv = (uint32_t)w[h];
+        const uint32_t known = lu & lv;
+        const uint32_t c = (lu & ~lv) | ((known && tau < (uint32_t)(w[h] >> 32)) ? known : 0u);
+        cm |= (unsigned long long)c << (32 * h);
+    }
+    return cm;
+}
+
+// Lanes `lanes` of half h reach v for the first time with arrival tau: add them to the half's
+// word and raise its bound to tau.  Every successful exchange adds a lane or raises the bound of
+// at most 32 lanes' first arrivals, so the loop ends; the cap only guards it.
+__device__ __forceinline__ void reached_add(unsigned long long *p, uint32_t lanes, uint32_t tau) {
+    unsigned long long old = __ldcg(p);
+    for (int k = 0; k < 4096; ++k) {
+        const uint32_t b = (uint32_t)(old >> 32);
+        const unsigned long long nw = ((unsigned long long)(b > tau ? b : tau) << 32) | ((uint32_t)old | lanes);
+        if (nw == old) return;
+        const unsigned long long prev = atomicCAS(p, old, nw);
+        if (prev == old) return;
+        old = prev;
+    }
 }
 
 // Relax up to ST_G edges g < cnt (into head v[g], departure t[g], arrival tau[g]) in every lane,
-// given each edge's tail thresholds thr[g][.]; the warp takes part as a whole.  The head rows of
-// all edges with a usable lane are loaded together, then each is lowered where the arrival is
-// earlier.  Lanes that reach v for the first time raise rmax[v] and then join rmask[v]; a drop
-// lowers minrow[v] and queues v for this block's fix-ups when the arrival is below tend.
-template <int W>
+// given each edge's tail thresholds thr[g][.]; the warp takes part as a whole.  With PRE the
+// head labels hv[g][.] of the candidate lanes come loaded together with the tails'; otherwise
+// the head rows of all edges with a usable lane are loaded here.  PASS: called from a block's
+// pass (queue entries are taken only after the grid barrier that ends it).  Each is lowered
+// where the arrival is earlier.  Lanes that reach v for the first time join v's reached-lane
+// summary with the arrival as bound; a drop lowers minrow[v] and queues v for this block's
+// fix-ups when the arrival
+// is below tend.
+template <int W, bool PASS, bool PRE, bool D>
 __device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLaneReg<W> &R, int lane, int cnt,
-                                            const uint32_t (&thr)[ST_G][W / 32], const int32_t (&v)[ST_G],
-                                            const uint32_t (&t)[ST_G], const uint32_t (&tau)[ST_G],
-                                            const unsigned long long (&cm)[ST_G], uint32_t tend, int32_t *fq,
-                                            unsigned *fcount) {
+                                            const uint32_t (&thr)[ST_G][W / 32], const uint32_t (&hv)[ST_G][W / 32],
+                                            const int32_t (&v)[ST_G], const uint32_t (&t)[ST_G],
+                                            const uint32_t (&tau)[ST_G], const unsigned long long (&cm)[ST_G],
+                                            uint32_t tend, int32_t *fq, unsigned *fcount) {
     constexpr int LPT = W / 32;
     bool adm[ST_G][LPT];
     unsigned anyg = 0;
@@ -101,12 +156,12 @@ __device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLan
         if (__any_sync(SFULL, any)) anyg |= 1u << g;
     }
     if (!anyg) return;
-    uint32_t c[ST_G][LPT];
+    uint32_t c[ST_G][LPT];  // head labels: may be stale, never below the label
 #pragma unroll
     for (int g = 0; g < ST_G; ++g)
 #pragma unroll
-        for (int i = 0; i < LPT; ++i)  // only the lanes that may drop: may be stale, never below the label
-            c[g][i] = adm[g][i] ? __ldcg(a.arr + (size_t)v[g] * W + lane + 32 * i) : 0u;
+        for (int i = 0; i < LPT; ++i)
+            c[g][i] = !adm[g][i] ? 0u : PRE ? hv[g][i] : __ldcg(a.arr + (size_t)v[g] * W + lane + 32 * i);
 #pragma unroll
     for (int g = 0; g < ST_G; ++g) {
         if (!((anyg >> g) & 1u)) continue;
@@ -117,20 +172,22 @@ __device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLan
             const bool d = adm[g][i] && tau[g] < c[g][i];
             if (d) {
                 atomicMin(a.arr + (size_t)v[g] * W + lane + 32 * i, tau[g]);  // a reduction: result unused
+                if (D) atomicAdd(&diag_counts()[6], 1ull);  // diagnostics
                 imp = true;
             }
             first |= (unsigned long long)__ballot_sync(SFULL, d && c[g][i] == INF) << (32 * i);
         }
         const bool dropped = __any_sync(SFULL, imp);
+        if (D && lane == 0 && dropped) atomicAdd(&diag_counts()[5], 1ull);  // diagnostics
+        if (!PASS) __syncwarp();  // the lanes' lowered labels precede lane 0's queue entry (below)
         if (lane == 0 && dropped) {
-            if (first) {
-                atomicMax(&a.rmax[v[g]], tau[g]);
-                __threadfence();  // the bound is visible before the lanes that need it
-                atomicOr(&a.rmask[v[g]], first);
-            }
+            if ((uint32_t)first) reached_add(&a.rsum[2 * (size_t)v[g]], (uint32_t)first, tau[g]);
+            if (first >> 32) reached_add(&a.rsum[2 * (size_t)v[g] + 1], (uint32_t)(first >> 32), tau[g]);
             atomicMin(&a.minrow[v[g]], tau[g]);
             if (tau[g] < tend) {
-                __threadfence();  // the lowered labels precede the queue entry
+                // a fix-up's queue entry is taken in the same round by a warp that then reads the
+                // labels; a pass's entries only after the grid barrier that ends the pass
+                if (!PASS) __threadfence();
                 const uint32_t bit = 1u << (v[g] & 31);
                 if (!(atomicOr(&a.fbm[v[g] >> 5], bit) & bit)) fq[atomicAdd(fcount, 1u)] = v[g];
             }
@@ -172,6 +229,8 @@ struct StreamCand {
 
 struct StreamSmem {
     int flag;
+    unsigned F;              // the current fix-up frontier length (read by thread 0)
+    unsigned next_tile;      // the block's next pass tile
     unsigned bcount[2];      // pooled candidates of the current block tile (by tile parity)
     uint32_t tile[32 * 65];  // readout transpose: 32 vertices x up to 64 lanes (+1 pad)
     StreamCand cand;
@@ -199,7 +258,7 @@ __device__ __forceinline__ int cand_push(StreamCand &L, int off, int len, int la
 // One fix-up vertex u, by one warp: its out-edges departing in [max(its least threshold, tbeg),
 // tend) (binary searches in the time-sorted list), filtered by the reached-lane bounds and
 // relaxed in batches; heads that drop below tend join the queue nq.
-template <int W, typename LamT>
+template <int W, typename LamT, bool D>
 __device__ __forceinline__ void fix_vertex(const StreamArgs &a, const StreamLaneReg<W> &R, int lane, StreamCand &L,
                                            int loff, int32_t u, uint32_t tbeg, uint32_t tend, uint32_t twmax,
                                            int32_t *nq, unsigned *ncount, unsigned long long &fixe) {
@@ -248,7 +307,7 @@ __device__ __forceinline__ void fix_vertex(const StreamArgs &a, const StreamLane
                 ++fixe;
                 ok = tau <= twmax;
             }
-            len = cand_push(L, loff, len, lane, ok ? may_improve(a, lanes_u, d, tau) : 0ull, u, d, tt, tau);
+            len = cand_push(L, loff, len, lane, ok ? may_improve<W>(a, lanes_u, d, tau) : 0ull, u, d, tt, tau);
         }
         __syncwarp();
         for (int base = 0; base < len; base += ST_G) {
@@ -264,7 +323,7 @@ __device__ __forceinline__ void fix_vertex(const StreamArgs &a, const StreamLane
                 t[g] = L.t[k2];
                 tau[g] = L.tau[k2];
             }
-            relax_batch<W>(a, R, lane, cnt, thr, v, t, tau, cm, tend, nq, ncount);
+            relax_batch<W, false, false, D>(a, R, lane, cnt, thr, thr, v, t, tau, cm, tend, nq, ncount);
         }
         __syncwarp();
     }
@@ -276,7 +335,8 @@ __device__ __forceinline__ void fix_vertex(const StreamArgs &a, const StreamLane
 constexpr unsigned ST_LOCAL_FIX = 16;
 constexpr unsigned ST_LOCAL_ROUNDS = 64;
 
-template <int W, typename LamT>
+// D: diagnostics (StreamArgs::phase_clock): phase cycle sums and candidate counts.
+template <int W, typename LamT, bool D>
 __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs a) {
     constexpr int LPT = W / 32;
     __shared__ StreamSmem S;
@@ -300,12 +360,13 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
     }
     for (int q = 0; q < a.lanes.nlanes; ++q) twmax = max(twmax, a.lanes.tw[q]);
 
+    if (threadIdx.x < 8) diag_counts()[threadIdx.x] = 0ull;
     // ---- initial labels (Alg. 2: t[x] = window start, every other label infinite) ----
     for (size_t i = tid; i < (size_t)n * W; i += nthr) a.arr[i] = INF;
     for (size_t i = tid; i < (size_t)n; i += nthr) {
         a.minrow[i] = INF;
-        a.rmask[i] = 0ull;
-        a.rmax[i] = 0u;
+        a.rsum[2 * i] = 0ull;
+        a.rsum[2 * i + 1] = 0ull;
     }
     for (size_t i = tid; i < nwords; i += nthr) a.fbm[i] = 0u;
     if (threadIdx.x == 0) S.bcount[0] = S.bcount[1] = 0;
@@ -314,24 +375,27 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
         const int q = threadIdx.x;
         a.arr[(size_t)a.lanes.src[q] * W + q] = a.lanes.ta[q];
         atomicMin(&a.minrow[a.lanes.src[q]], a.lanes.ta[q]);
-        atomicMax(&a.rmax[a.lanes.src[q]], a.lanes.ta[q]);
-        atomicOr(&a.rmask[a.lanes.src[q]], 1ull << q);
+        reached_add(&a.rsum[2 * (size_t)a.lanes.src[q] + (q >> 5)], 1u << (q & 31), a.lanes.ta[q]);
     }
     if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) return;
 
-    unsigned long long scanned = 0, cand = 0, fixe = 0, fixv = 0;
+    unsigned long long cand = 0, fixe = 0, fixv = 0;
     unsigned gen = 0, fix_rounds = 0;
+    unsigned nread = 0;  // frontier-length reads per block so far (the same in every block)
+    unsigned runs = 0;   // one-block fix-up runs so far (the same in every block)
     unsigned par = 0;  // parity of the block's pass tiles (selects the pooled candidate count)
+    // phases: 0 pass (reading and filtering records), 1 fix-ups, 2 grid barriers, initialisation
+    // and read-out, 3 the passes' candidate relaxations
     unsigned long long ph[4] = {0, 0, 0, 0};
-    long long ph_last = a.phase_clock ? clock64() : 0;
+    long long ph_last = D ? clock64() : 0;
     auto mark = [&](int p) {
-        if (a.phase_clock) {
+        if (D) {
             const long long now = clock64();
             ph[p] += (unsigned long long)(now - ph_last);
             ph_last = now;
         }
     };
-    mark(3);
+    mark(2);
     for (int k = a.k_begin; k < a.k_end; ++k) {
         const uint64_t lo = a.bnd[k], hi = a.bnd[k + 1];
         const uint32_t tbeg = a.bt[k], tend = a.bt[k + 1];
@@ -339,10 +403,21 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
         // records at a time (KE per thread); the candidates of that tile are pooled and dealt to
         // its warps in batches, so that a warp whose records hold many does not hold the round.
         {
-            int32_t *fq = a.fq[gen & 1];
-            unsigned *fcount = &C->fcount[gen % 3].v;
+            // the pass is generation gen: like a fix-up round it appends to slot gen + 1 and
+            // clears slot gen + 2, so that a block still reading slot gen (the frontier length that
+            // ended the last time block's rounds) is not disturbed by blocks already here
+            int32_t *fq = a.fq[(gen + 1) & 1];
+            unsigned *fcount = &C->fcount[(gen + 1) % 3].v;
+            if (tid == 0) C->fcount[(gen + 2) % 3].v = 0;
             const int wib = threadIdx.x >> 5;
-            for (uint64_t tb = lo + (uint64_t)blockIdx.x * ST_CAND; tb < hi; tb += (uint64_t)gridDim.x * ST_CAND, par ^= 1u) {
+            // tiles dealt dynamically: the block's first is its own index, each later one is
+            // claimed (one atomic by thread 0, issued a tile ahead) so that blocks whose tiles
+            // hold few candidates take more of them
+            if (tid == 0) C->claim[(k + 1) & 1].v = 0;  // the next time block's counter (last used two blocks ago)
+            const unsigned ntiles = (unsigned)((hi - lo + ST_CAND - 1) / ST_CAND);
+            for (unsigned ti = blockIdx.x; ti < ntiles; par ^= 1u) {
+                if (threadIdx.x == 0) S.next_tile = gridDim.x + atomicAdd(&C->claim[k & 1].v, 1u);
+                const uint64_t tb = lo + (uint64_t)ti * ST_CAND;
                 StreamRec r[ST_KE];
                 bool c[ST_KE];
 #pragma unroll
@@ -355,7 +430,6 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                         r[j].dst = x.y;
                         r[j].t = (uint32_t)x.z;
                         r[j].lam = (uint32_t)x.w;
-                        ++scanned;
                     } else {
                         r[j].src = r[j].dst = 0;
                         r[j].t = r[j].lam = 0;
@@ -366,18 +440,18 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
 #pragma unroll
                 for (int j = 0; j < ST_KE; ++j) {
                     mn[j] = c[j] ? __ldcg(&a.minrow[r[j].src]) : INF;
-                    lu[j] = c[j] ? __ldcg(&a.rmask[r[j].src]) : 0ull;
+                    lu[j] = c[j] ? reached_lanes<W>(a, r[j].src) : 0ull;
                 }
                 unsigned *cntp = &S.bcount[par];
 #pragma unroll
                 for (int j = 0; j < ST_KE; ++j) {
                     const uint32_t tau = r[j].t + r[j].lam;
                     const bool ok = c[j] && r[j].t >= mn[j] && tau <= twmax && lu[j] != 0ull;
-                    const unsigned long long cmj = ok ? may_improve(a, lu[j], r[j].dst, tau) : 0ull;
-                    if (a.phase_clock && cmj) {  // diagnostics: how many lanes a candidate carries
+                    const unsigned long long cmj = ok ? may_improve<W>(a, lu[j], r[j].dst, tau) : 0ull;
+                    if (D && cmj) {  // diagnostics: how many lanes a candidate carries
                         const int pc = __popcll(cmj);
-                        atomicAdd(&C->cand_lanes[pc == 1 ? 0 : pc <= 4 ? 1 : pc <= 16 ? 2 : 3], 1ull);
-                        atomicAdd(&C->cand_pairs, (unsigned long long)pc);
+                        atomicAdd(&diag_counts()[pc == 1 ? 0 : pc <= 4 ? 1 : pc <= 16 ? 2 : 3], 1ull);
+                        atomicAdd(&diag_counts()[4], (unsigned long long)pc);
                     }
                     const unsigned m = __ballot_sync(SFULL, cmj != 0ull);
                     unsigned pos = 0;
@@ -386,6 +460,8 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                     if (cmj) cand_put(S.cand, (int)pos, cmj, r[j].src, r[j].dst, r[j].t, tau);
                 }
                 __syncthreads();
+                mark(0);
+                ti = S.next_tile;  // read before the tile's last barrier, after which it is rewritten
                 const int len = (int)*cntp;
                 if (threadIdx.x == 0) S.bcount[par ^ 1u] = 0;  // the next tile's count (unused until then)
                 cand += (threadIdx.x == 0) ? len : 0;
@@ -404,12 +480,18 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                         t[g] = L.t[k2];
                         tau[g] = L.tau[k2];
                     }
+                    // the tails' labels in the candidate lanes, all in flight together, and with 32
+                    // lanes the heads' labels as well (with 64, the registers of both would spill)
+                    constexpr bool PRE = W == 32;
+                    uint32_t hv[ST_G][LPT];
 #pragma unroll
-                    for (int g = 0; g < ST_G; ++g)  // the tails' labels in the candidate lanes, all in flight together
+                    for (int g = 0; g < ST_G; ++g)
 #pragma unroll
-                        for (int i = 0; i < LPT; ++i)
-                            thr[g][i] = ((cm[g] >> (lane + 32 * i)) & 1ull) ? __ldcg(a.arr + (size_t)u[g] * W + lane + 32 * i)
-                                                                            : INF;
+                        for (int i = 0; i < LPT; ++i) {
+                            const bool on = (cm[g] >> (lane + 32 * i)) & 1ull;
+                            thr[g][i] = on ? __ldcg(a.arr + (size_t)u[g] * W + lane + 32 * i) : INF;
+                            hv[g][i] = (PRE && on && tau[g] <= R.tw[i]) ? __ldcg(a.arr + (size_t)v[g] * W + lane + 32 * i) : 0u;
+                        }
 #pragma unroll
                     for (int g = 0; g < ST_G; ++g)
 #pragma unroll
@@ -417,8 +499,9 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                             const uint32_t x = thr[g][i];
                             thr[g][i] = (R.on[i] && x != INF) ? x + ((R.strict[i] && u[g] != R.src[i]) ? 1u : 0u) : INF;
                         }
-                    relax_batch<W>(a, R, lane, cnt, thr, v, t, tau, cm, tend, fq, fcount);
+                    relax_batch<W, true, PRE, D>(a, R, lane, cnt, thr, hv, v, t, tau, cm, tend, fq, fcount);
                 }
+                mark(3);
                 __syncthreads();  // the list is rewritten by the next tile
             }
         }
@@ -431,9 +514,19 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
             return;
         }
         mark(2);
+        ++gen;  // the pass's queue is the first fix-up frontier
         // ---- fix-ups: frontier rounds over the block's departures ----
         for (unsigned round = 0;; ++round) {
-            const unsigned F = __ldcg(&C->fcount[gen % 3].v);
+            // the frontier length, read once per block; the read is counted so that a one-block
+            // run (below) resets this slot only after every block has read it
+            if (threadIdx.x == 0) {
+                S.F = __ldcg(&C->fcount[gen % 3].v);
+                __threadfence();
+                atomicAdd(&C->fread, 1ull);
+            }
+            __syncthreads();
+            const unsigned F = S.F;
+            ++nread;
             if (F == 0) break;
             if (round >= a.max_fix_rounds) {
                 if (tid == 0) atomicCAS(&C->err, 0, KERR_FIX_ROUNDS);
@@ -446,11 +539,24 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                 if (blockIdx.x == 0) {
                     unsigned g2 = gen, f = F, rr = round;
                     while (f != 0 && f <= ST_LOCAL_FIX && rr < a.max_fix_rounds && rr - round < ST_LOCAL_ROUNDS) {
-                        if (threadIdx.x == 0) C->fcount[(g2 + 2) % 3].v = 0;
+                        if (threadIdx.x == 0) {
+                            if (g2 == gen + 1) {  // about to reset slot gen % 3: wait for its readers
+                                const unsigned long long want = (unsigned long long)gridDim.x * nread;
+                                unsigned long long spins = 0;
+                                while (ld_acquire64(&C->fread) < want) {
+                                    if (++spins > a.spin_limit) {
+                                        atomicCAS(&C->err, 0, KERR_BARRIER_TIMEOUT);
+                                        break;
+                                    }
+                                    __nanosleep(64);
+                                }
+                            }
+                            C->fcount[(g2 + 2) % 3].v = 0;
+                        }
                         const int32_t *cq = a.fq[g2 & 1];
                         for (unsigned idx = threadIdx.x >> 5; idx < f; idx += ST_THREADS / 32) {
                             ++fixv;
-                            fix_vertex<W, LamT>(a, R, lane, S.cand, loff, __ldcg(&cq[idx]), tbeg, tend, twmax,
+                            fix_vertex<W, LamT, D>(a, R, lane, S.cand, loff, __ldcg(&cq[idx]), tbeg, tend, twmax,
                                                 a.fq[(g2 + 1) & 1], &C->fcount[(g2 + 1) % 3].v, fixe);
                         }
                         __threadfence();
@@ -462,8 +568,8 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                         __syncthreads();  // every thread has read f before the next reset
                     }
                     if (threadIdx.x == 0) {
-                        C->gen_shared = g2;
-                        C->round_shared = rr;
+                        C->gen_shared[runs & 1] = g2;
+                        C->round_shared[runs & 1] = rr;
                     }
                 }
                 mark(1);
@@ -475,8 +581,9 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                     return;
                 }
                 mark(2);
-                gen = __ldcg(&C->gen_shared);
-                round = __ldcg(&C->round_shared) - 1;  // the loop adds one
+                gen = __ldcg(&C->gen_shared[runs & 1]);
+                round = __ldcg(&C->round_shared[runs & 1]) - 1;  // the loop adds one
+                ++runs;
                 continue;
             }
             if (tid == 0) C->fcount[(gen + 2) % 3].v = 0;
@@ -486,7 +593,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
             unsigned *ncount = &C->fcount[(gen + 1) % 3].v;
             for (unsigned idx = gw; idx < F; idx += nwarps) {  // queue entries dealt to warps in turn
                 ++fixv;
-                fix_vertex<W, LamT>(a, R, lane, S.cand, loff, __ldcg(&cq[idx]), tbeg, tend, twmax, nq, ncount, fixe);
+                fix_vertex<W, LamT, D>(a, R, lane, S.cand, loff, __ldcg(&cq[idx]), tbeg, tend, twmax, nq, ncount, fixe);
             }
             mark(1);
             if (!grid_sync(C, &S.flag, a.spin_limit, KERR_BARRIER_TIMEOUT)) {
@@ -535,24 +642,30 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
     for (int i = 0; i < LPT; ++i)
         if (R.on[i] && reached[i]) atomicAdd(&C->reached[lane + 32 * i], reached[i]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        scanned += __shfl_xor_sync(SFULL, scanned, o);
-        fixe += __shfl_xor_sync(SFULL, fixe, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) fixe += __shfl_xor_sync(SFULL, fixe, o);
     if (lane == 0) {
-        atomicAdd(&C->scanned, scanned + fixe);
+        atomicAdd(&C->scanned, fixe);
         atomicAdd(&C->fix_edges, fixe);
         atomicAdd(&C->cand, cand);
         atomicAdd(&C->fix_vertices, fixv);
     }
     if (tid == 0) {
+        atomicAdd(&C->scanned, (unsigned long long)(a.bnd[a.k_end] - a.bnd[a.k_begin]));  // each pass record once
         C->fix_rounds = fix_rounds;  // thread 0 counts the grid-wide and the one-block rounds
         C->blocks = (unsigned)(a.k_end - a.k_begin);
     }
-    mark(3);
-    if (a.phase_clock && lane == 0)
+    mark(2);
+    if (D) {
+        if (lane == 0)
 #pragma unroll
-        for (int p = 0; p < 4; ++p) atomicAdd(&C->phase_cycles[p], ph[p]);
+            for (int p = 0; p < 4; ++p) atomicAdd(&C->phase_cycles[p], ph[p]);
+        __syncthreads();
+        const unsigned long long *d = diag_counts();
+        if (threadIdx.x < 4) atomicAdd(&C->cand_lanes[threadIdx.x], d[threadIdx.x]);
+        if (threadIdx.x == 4) atomicAdd(&C->cand_pairs, d[4]);
+        if (threadIdx.x == 5) atomicAdd(&C->cand_improving, d[5]);
+        if (threadIdx.x == 6) atomicAdd(&C->lanes_lowered, d[6]);
+    }
 }
 
 // Relaxed edges per lane under the final labels (the TE of the query statistics): every
@@ -609,7 +722,8 @@ __global__ void __launch_bounds__(ST_THREADS) stream_count_kernel(const StreamAr
 template <int W, typename LamT>
 cudaError_t stream_launch_t(const StreamArgs &a, int grid, cudaStream_t s) {
     void *args[] = {(void *)&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)stream_kernel<W, LamT>, dim3(grid), dim3(ST_THREADS), args, 0, s);
+    void *fn = a.phase_clock ? (void *)stream_kernel<W, LamT, true> : (void *)stream_kernel<W, LamT, false>;
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(ST_THREADS), args, 0, s);
     if (e != cudaSuccess || !a.count_relaxed) return e;
     stream_count_kernel<W><<<grid, ST_THREADS, 0, s>>>(a);
     return cudaGetLastError();
@@ -618,9 +732,11 @@ cudaError_t stream_launch_t(const StreamArgs &a, int grid, cudaStream_t s) {
 template <int W, typename LamT>
 int stream_max_blocks_t() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stream_kernel<W, LamT>, ST_THREADS, 0) != cudaSuccess)
+    int nd = 0;  // the diagnostic form runs in the same launch shape
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stream_kernel<W, LamT, false>, ST_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd, stream_kernel<W, LamT, true>, ST_THREADS, 0) != cudaSuccess)
         return 0;
-    return nb;
+    return nb < nd ? nb : nd;
 }
 
 }  // namespace
