@@ -62,6 +62,9 @@ def parse():
     p.add_argument("--serve-queries", type=int, default=400)
     p.add_argument("--serve-slots", type=int, default=16)
     p.add_argument("--serve-slice", type=int, default=0, help="edge-map rounds per server launch (0: default)")
+    p.add_argument("--scale", type=int, default=0,
+                   help="run the workload's graph at 2^scale vertices, same edge factor and laws (small cases "
+                        "for profiling; not a bench line of the named configuration)")
     p.add_argument("--cpu-sample-edges", type=int, default=1 << 26,
                    help="edges of the oracle baseline's sample (the most recent departures)")
     return p.parse_args()
@@ -710,8 +713,12 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = synth.WORKLOADS[args.workload]
+    spec = w.graph
+    if args.scale:
+        spec = synth.scaled(w.graph, args.scale, w.graph.m >> max(0, w.graph.scale - args.scale))
+        args.no_extras = True
     t0 = time.perf_counter()
-    el = synth.rmat(w.graph)
+    el = synth.rmat(spec)
     gen_s = time.perf_counter() - t0
     queries = synth.workload_queries(args.workload, el, shard=rank)
     Q, n, m = len(queries), el.n, el.m
@@ -783,7 +790,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"{w.name}: {w.description}", "vertices": n, "edges": m, "queries_per_step": Q,
+        "config": {"workload": f"{w.name}: {w.description}" + (f" (scaled to 2^{args.scale} vertices)" if args.scale else ""),
+                   "vertices": n, "edges": m, "queries_per_step": Q,
                    "index_threshold": theta_now, **tuning_dict(tuning), "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (graph {2 * (m * R + 8 * n) / 1e9:.1f} GB)"},
         "queries_per_s": world * Q / (step_ms / 1e3),

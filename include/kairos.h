@@ -132,8 +132,10 @@ typedef struct {
                                and workspace with 1/concurrent of the resident blocks (unless
                                blocks_per_sm is set): 1 or 2 (0 means 1), or 4 with relax_mode 3.
                                More lets one launch's sparse rounds overlap another's busy ones; it
-                               applies when the outputs are device or page-locked host memory and
-                               the call has two or more launches */
+                               applies when the call has two or more launches and its outputs are
+                               device memory, or page-locked host memory with relax_mode 3 (each
+                               launch's rows are then staged on the device and copied to the host
+                               by the copy engine on the launch's stream) */
     int32_t block_edges;    /* relax_mode 3: edges per time block (an instant is never split);
                                0: max(4096, n_edges / 512) */
     int32_t select_permille; /* selective access (Sec. 5.1, Eq. 3) for the frontier modes 0-2:

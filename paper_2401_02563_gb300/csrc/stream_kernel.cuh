@@ -86,30 +86,34 @@ __device__ __forceinline__ unsigned long long reached_lanes(const StreamArgs &a,
     return (uint32_t)s.x | ((unsigned long long)(uint32_t)s.y << 32);
 }
 
-// The lanes of `lanes_u` (lanes where the tail is reached) in which an edge into v arriving at
-// tau can improve v: those not yet reached at v, plus, in a half whose bound is above tau, the
-// ones reached there.
+// The reached-lane words of vertex v (both halves; the second is zero with 32 lanes).
 template <int W>
-__device__ __forceinline__ unsigned long long may_improve(const StreamArgs &a, unsigned long long lanes_u, int32_t v,
-                                                          uint32_t tau) {
-    unsigned long long w[2];
-    if (W == 32) {
-        w[0] = __ldcg(&a.rsum[2 * (size_t)v]);
-        w[1] = 0ull;
-    } else {
-        const ulonglong2 s = __ldcg(reinterpret_cast<const ulonglong2 *>(a.rsum) + v);
-        w[0] = s.x;
-        w[1] = s.y;
-    }
+__device__ __forceinline__ ulonglong2 reached_words(const StreamArgs &a, int32_t v) {
+    if (W == 32) return make_ulonglong2(__ldcg(&a.rsum[2 * (size_t)v]), 0ull);
+    return __ldcg(reinterpret_cast<const ulonglong2 *>(a.rsum) + v);
+}
+
+// The lanes of `lanes_u` (lanes where the tail is reached) in which an edge into v arriving at
+// tau can improve v, given v's reached-lane words w: those not yet reached at v, plus, in a half
+// whose bound is above tau, the ones reached there.
+template <int W>
+__device__ __forceinline__ unsigned long long improvable(unsigned long long lanes_u, ulonglong2 w, uint32_t tau) {
     unsigned long long cm = 0ull;
 #pragma unroll
     for (int h = 0; h < W / 32; ++h) {
-        const uint32_t lu = (uint32_t)(lanes_u >> (32 * h)), lv = (uint32_t)w[h];
+        const unsigned long long x = h ? w.y : w.x;
+        const uint32_t lu = (uint32_t)(lanes_u >> (32 * h)), lv = (uint32_t)x;
         const uint32_t known = lu & lv;
-        const uint32_t c = (lu & ~lv) | ((known && tau < (uint32_t)(w[h] >> 32)) ? known : 0u);
+        const uint32_t c = (lu & ~lv) | ((known && tau < (uint32_t)(x >> 32)) ? known : 0u);
         cm |= (unsigned long long)c << (32 * h);
     }
     return cm;
+}
+
+template <int W>
+__device__ __forceinline__ unsigned long long may_improve(const StreamArgs &a, unsigned long long lanes_u, int32_t v,
+                                                          uint32_t tau) {
+    return improvable<W>(lanes_u, reached_words<W>(a, v), tau);
 }
 
 // Lanes `lanes` of half h reach v for the first time with arrival tau: add them to the half's
@@ -127,46 +131,46 @@ __device__ __forceinline__ void reached_add(unsigned long long *p, uint32_t lane
     }
 }
 
-// Relax up to ST_G edges g < cnt (into head v[g], departure t[g], arrival tau[g]) in every lane,
-// given each edge's tail thresholds thr[g][.]; the warp takes part as a whole.  With PRE the
-// head labels hv[g][.] of the candidate lanes come loaded together with the tails'; otherwise
-// the head rows of all edges with a usable lane are loaded here.  PASS: called from a block's
-// pass (queue entries are taken only after the grid barrier that ends it).  Each is lowered
-// where the arrival is earlier.  Lanes that reach v for the first time join v's reached-lane
-// summary with the arrival as bound; a drop lowers minrow[v] and queues v for this block's
-// fix-ups when the arrival
-// is below tend.
-template <int W, bool PASS, bool PRE, bool D>
+// Relax up to G edges g < cnt (into head v[g], departure t[g], arrival tau[g]) in every lane,
+// given each edge's tail thresholds thr[g][.] and on[g] (bit i: this thread's lane lane + 32 i is
+// a candidate lane of the edge); the warp takes part as a whole.  With PRE the head labels
+// hv[g][.] of the candidate lanes come loaded together with the tails'; otherwise the head rows
+// of all edges with a usable lane are loaded here.  PASS: called from a block's pass (queue
+// entries are taken only after the grid barrier that ends it).  Each label is lowered where the
+// arrival is earlier; then lane g updates head g's summaries: lanes reached for the first time
+// join its reached-lane word with the arrival as bound, minrow drops, and the head is queued for
+// this block's fix-ups when the arrival is below tend.
+template <int W, bool PASS, bool PRE, bool D, int G = ST_G>
 __device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLaneReg<W> &R, int lane, int cnt,
-                                            const uint32_t (&thr)[ST_G][W / 32], const uint32_t (&hv)[ST_G][W / 32],
-                                            const int32_t (&v)[ST_G], const uint32_t (&t)[ST_G],
-                                            const uint32_t (&tau)[ST_G], const unsigned long long (&cm)[ST_G],
-                                            uint32_t tend, int32_t *fq, unsigned *fcount) {
+                                            const uint32_t (&thr)[G][W / 32], const uint32_t (&hv)[G][W / 32],
+                                            const int32_t (&v)[G], const uint32_t (&t)[G], const uint32_t (&tau)[G],
+                                            const unsigned (&on)[G], uint32_t tend, int32_t *fq, unsigned *fcount) {
     constexpr int LPT = W / 32;
-    bool adm[ST_G][LPT];
+    bool adm[G][LPT];
     unsigned anyg = 0;
 #pragma unroll
-    for (int g = 0; g < ST_G; ++g) {
+    for (int g = 0; g < G; ++g) {
         bool any = false;
 #pragma unroll
         for (int i = 0; i < LPT; ++i) {
-            adm[g][i] = g < cnt && ((cm[g] >> (lane + 32 * i)) & 1ull) && thr[g][i] <= t[g] && tau[g] <= R.tw[i];
+            adm[g][i] = g < cnt && ((on[g] >> i) & 1u) && thr[g][i] <= t[g] && tau[g] <= R.tw[i];
             any |= adm[g][i];
         }
         if (__any_sync(SFULL, any)) anyg |= 1u << g;
     }
     if (!anyg) return;
-    uint32_t c[ST_G][LPT];  // head labels: may be stale, never below the label
+    uint32_t c[G][LPT];  // head labels: may be stale, never below the label
 #pragma unroll
-    for (int g = 0; g < ST_G; ++g)
+    for (int g = 0; g < G; ++g)
 #pragma unroll
         for (int i = 0; i < LPT; ++i)
             c[g][i] = !adm[g][i] ? 0u : PRE ? hv[g][i] : __ldcg(a.arr + (size_t)v[g] * W + lane + 32 * i);
+    // lower the labels; per edge g the lanes reached for the first time, by half
+    uint32_t fh[G][LPT];
+    unsigned dmask = 0;  // edges that lowered some label
 #pragma unroll
-    for (int g = 0; g < ST_G; ++g) {
-        if (!((anyg >> g) & 1u)) continue;
+    for (int g = 0; g < G; ++g) {
         bool imp = false;
-        unsigned long long first = 0;  // lanes reaching v for the first time
 #pragma unroll
         for (int i = 0; i < LPT; ++i) {
             const bool d = adm[g][i] && tau[g] < c[g][i];
@@ -175,22 +179,34 @@ __device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLan
                 if (D) atomicAdd(&diag_counts()[6], 1ull);  // diagnostics
                 imp = true;
             }
-            first |= (unsigned long long)__ballot_sync(SFULL, d && c[g][i] == INF) << (32 * i);
+            fh[g][i] = __ballot_sync(SFULL, d && c[g][i] == INF);
         }
-        const bool dropped = __any_sync(SFULL, imp);
-        if (D && lane == 0 && dropped) atomicAdd(&diag_counts()[5], 1ull);  // diagnostics
-        if (!PASS) __syncwarp();  // the lanes' lowered labels precede lane 0's queue entry (below)
-        if (lane == 0 && dropped) {
-            if ((uint32_t)first) reached_add(&a.rsum[2 * (size_t)v[g]], (uint32_t)first, tau[g]);
-            if (first >> 32) reached_add(&a.rsum[2 * (size_t)v[g] + 1], (uint32_t)(first >> 32), tau[g]);
-            atomicMin(&a.minrow[v[g]], tau[g]);
-            if (tau[g] < tend) {
-                // a fix-up's queue entry is taken in the same round by a warp that then reads the
-                // labels; a pass's entries only after the grid barrier that ends the pass
-                if (!PASS) __threadfence();
-                const uint32_t bit = 1u << (v[g] & 31);
-                if (!(atomicOr(&a.fbm[v[g] >> 5], bit) & bit)) fq[atomicAdd(fcount, 1u)] = v[g];
+        if (__any_sync(SFULL, imp)) dmask |= 1u << g;
+    }
+    if (!dmask) return;
+    if (D && lane == 0) atomicAdd(&diag_counts()[5], (unsigned long long)__popc(dmask));  // diagnostics
+    __syncwarp();  // the lanes' lowered labels precede the queue entries (below)
+    // head summaries and fix-up queue: lane g for edge g, the edges' atomics in flight together
+    if (lane < G && ((dmask >> lane) & 1u)) {
+        int32_t vg = v[0];
+        uint32_t tg = tau[0], f0 = fh[0][0], f1 = LPT > 1 ? fh[0][LPT - 1] : 0u;
+#pragma unroll
+        for (int g = 1; g < G; ++g)
+            if (lane == g) {
+                vg = v[g];
+                tg = tau[g];
+                f0 = fh[g][0];
+                f1 = LPT > 1 ? fh[g][LPT - 1] : 0u;
             }
+        if (f0) reached_add(&a.rsum[2 * (size_t)vg], f0, tg);
+        if (f1) reached_add(&a.rsum[2 * (size_t)vg + 1], f1, tg);
+        atomicMin(&a.minrow[vg], tg);
+        if (tg < tend) {
+            // a fix-up's queue entry is taken in the same round by a warp that then reads the
+            // labels; a pass's entries only after the grid barrier that ends the pass
+            if (!PASS) __threadfence();
+            const uint32_t bit = 1u << (vg & 31);
+            if (!(atomicOr(&a.fbm[vg >> 5], bit) & bit)) fq[atomicAdd(fcount, 1u)] = vg;
         }
     }
 }
@@ -314,16 +330,19 @@ __device__ __forceinline__ void fix_vertex(const StreamArgs &a, const StreamLane
             const int cnt = min(ST_G, len - base);
             int32_t v[ST_G];
             uint32_t t[ST_G], tau[ST_G];
-            unsigned long long cm[ST_G];
+            unsigned on[ST_G];  // bit i: this thread's lane lane + 32 i is a candidate lane of edge g
 #pragma unroll
             for (int g = 0; g < ST_G; ++g) {
                 const int k2 = loff + base + (g < cnt ? g : 0);
-                cm[g] = g < cnt ? L.cm[k2] : 0ull;
+                const unsigned long long cm = g < cnt ? L.cm[k2] : 0ull;
+                on[g] = 0u;
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) on[g] |= (unsigned)((cm >> (lane + 32 * i)) & 1ull) << i;
                 v[g] = L.v[k2];
                 t[g] = L.t[k2];
                 tau[g] = L.tau[k2];
             }
-            relax_batch<W, false, false, D>(a, R, lane, cnt, thr, thr, v, t, tau, cm, tend, nq, ncount);
+            relax_batch<W, false, false, D>(a, R, lane, cnt, thr, thr, v, t, tau, on, tend, nq, ncount);
         }
         __syncwarp();
     }
@@ -435,19 +454,22 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                         r[j].t = r[j].lam = 0;
                     }
                 }
+                // the tails' summaries and the heads' reached-lane words, all in flight together
                 uint32_t mn[ST_KE];
                 unsigned long long lu[ST_KE];
+                ulonglong2 hw[ST_KE];
 #pragma unroll
                 for (int j = 0; j < ST_KE; ++j) {
                     mn[j] = c[j] ? __ldcg(&a.minrow[r[j].src]) : INF;
                     lu[j] = c[j] ? reached_lanes<W>(a, r[j].src) : 0ull;
+                    hw[j] = c[j] ? reached_words<W>(a, r[j].dst) : make_ulonglong2(0ull, 0ull);
                 }
                 unsigned *cntp = &S.bcount[par];
 #pragma unroll
                 for (int j = 0; j < ST_KE; ++j) {
                     const uint32_t tau = r[j].t + r[j].lam;
                     const bool ok = c[j] && r[j].t >= mn[j] && tau <= twmax && lu[j] != 0ull;
-                    const unsigned long long cmj = ok ? may_improve<W>(a, lu[j], r[j].dst, tau) : 0ull;
+                    const unsigned long long cmj = ok ? improvable<W>(lu[j], hw[j], tau) : 0ull;
                     if (D && cmj) {  // diagnostics: how many lanes a candidate carries
                         const int pc = __popcll(cmj);
                         atomicAdd(&diag_counts()[pc == 1 ? 0 : pc <= 4 ? 1 : pc <= 16 ? 2 : 3], 1ull);
@@ -466,40 +488,42 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                 if (threadIdx.x == 0) S.bcount[par ^ 1u] = 0;  // the next tile's count (unused until then)
                 cand += (threadIdx.x == 0) ? len : 0;
                 StreamCand &L = S.cand;
-                for (int base = wib * ST_G; base < len; base += (ST_THREADS / 32) * ST_G) {
-                    const int cnt = min(ST_G, len - base);
-                    int32_t u[ST_G], v[ST_G];
-                    uint32_t t[ST_G], tau[ST_G], thr[ST_G][LPT];
-                    unsigned long long cm[ST_G];
+                // edges per batch: four, or three with 64 lanes (register budget of the preloads)
+                constexpr int G = W == 64 ? 3 : ST_G;
+                for (int base = wib * G; base < len; base += (ST_THREADS / 32) * G) {
+                    const int cnt = min(G, len - base);
+                    int32_t v[G];
+                    uint32_t t[G], tau[G], thr[G][LPT], hv[G][LPT];
+                    // per edge: bit i = lane lane + 32 i is a candidate lane, bit 2 + i = the tail
+                    // is not that lane's source (StrictlySucceeds adds one there)
+                    unsigned on[G];
+                    // the tails' and heads' labels in the candidate lanes, all in flight together
 #pragma unroll
-                    for (int g = 0; g < ST_G; ++g) {
+                    for (int g = 0; g < G; ++g) {
                         const int k2 = base + (g < cnt ? g : 0);
-                        cm[g] = g < cnt ? L.cm[k2] : 0ull;
-                        u[g] = L.u[k2];
+                        const unsigned long long cm = g < cnt ? L.cm[k2] : 0ull;
+                        const int32_t u = L.u[k2];
                         v[g] = L.v[k2];
                         t[g] = L.t[k2];
                         tau[g] = L.tau[k2];
-                    }
-                    // the tails' labels in the candidate lanes, all in flight together, and with 32
-                    // lanes the heads' labels as well (with 64, the registers of both would spill)
-                    constexpr bool PRE = W == 32;
-                    uint32_t hv[ST_G][LPT];
-#pragma unroll
-                    for (int g = 0; g < ST_G; ++g)
+                        on[g] = 0u;
 #pragma unroll
                         for (int i = 0; i < LPT; ++i) {
-                            const bool on = (cm[g] >> (lane + 32 * i)) & 1ull;
-                            thr[g][i] = on ? __ldcg(a.arr + (size_t)u[g] * W + lane + 32 * i) : INF;
-                            hv[g][i] = (PRE && on && tau[g] <= R.tw[i]) ? __ldcg(a.arr + (size_t)v[g] * W + lane + 32 * i) : 0u;
+                            const bool c1 = (cm >> (lane + 32 * i)) & 1ull;
+                            on[g] |= (c1 ? 1u : 0u) << i;
+                            on[g] |= ((R.strict[i] && u != R.src[i]) ? 4u : 0u) << i;
+                            thr[g][i] = c1 ? __ldcg(a.arr + (size_t)u * W + lane + 32 * i) : INF;
+                            hv[g][i] = (c1 && tau[g] <= R.tw[i]) ? __ldcg(a.arr + (size_t)v[g] * W + lane + 32 * i) : 0u;
                         }
+                    }
 #pragma unroll
-                    for (int g = 0; g < ST_G; ++g)
+                    for (int g = 0; g < G; ++g)
 #pragma unroll
                         for (int i = 0; i < LPT; ++i) {
                             const uint32_t x = thr[g][i];
-                            thr[g][i] = (R.on[i] && x != INF) ? x + ((R.strict[i] && u[g] != R.src[i]) ? 1u : 0u) : INF;
+                            thr[g][i] = (R.on[i] && x != INF) ? x + ((on[g] >> (2 + i)) & 1u) : INF;
                         }
-                    relax_batch<W, true, PRE, D>(a, R, lane, cnt, thr, hv, v, t, tau, cm, tend, fq, fcount);
+                    relax_batch<W, true, true, D, G>(a, R, lane, cnt, thr, hv, v, t, tau, on, tend, fq, fcount);
                 }
                 mark(3);
                 __syncthreads();  // the list is rewritten by the next tile
