@@ -432,16 +432,17 @@ int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uin
  * environment.  Returns 8, or 0 on a NULL argument.  Diagnostic only. */
 int32_t kairos_last_phase_cycles(const kairos_graph *g, uint64_t *cycles8);
 
-/* Counters of the last time-ordered (relax_mode 3) launch on g: out17 = {time blocks swept,
+/* Counters of the last time-ordered (relax_mode 3) launch on g: out23 = {time blocks swept,
  * fix-up rounds, fix-up vertices, edges read by fix-ups, records whose lanes were examined,
  * records and edges read in all, then SM cycles summed over warps in block passes (reading and
  * filtering records), fix-ups, grid barriers with initialisation and read-out, and the passes'
  * candidate relaxations, then the pass's candidate records with 1, 2-4, 5-16 and 17-64
  * candidate lanes, the candidate lanes in all, the candidates (pass and fix-ups) that lowered
- * some label and the labels lowered (the cycles and the counts from the lane counts on are zero
- * unless the process ran with KAIROS_PHASE_CLOCK=1)}.  Returns 17, or 0 on a NULL argument.
- * Diagnostic only. */
-int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out17);
+ * some label, the labels lowered, then thread block 0's wall time (ns) in passes, grid-wide
+ * fix-up rounds and one-block fix-up runs, each with its closing grid barrier, and the number
+ * of each (the cycles and everything from the lane counts on are zero unless the process ran
+ * with KAIROS_PHASE_CLOCK=1)}.  Returns 23, or 0 on a NULL argument.  Diagnostic only. */
+int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out23);
 
 #ifdef __cplusplus
 }

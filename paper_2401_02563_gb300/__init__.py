@@ -575,7 +575,8 @@ def kairos_last_phase_cycles(g):
 STREAM_COUNTERS = ("blocks", "fix_rounds", "fix_vertices", "fix_edges", "candidates", "scanned",
                    "pass_filter_cycles", "fixup_cycles", "barrier_init_readout_cycles", "pass_relax_cycles",
                    "cand_1_lane", "cand_2_4_lanes", "cand_5_16_lanes", "cand_17_64_lanes", "cand_lanes",
-                   "cand_improving", "lanes_lowered")
+                   "cand_improving", "lanes_lowered", "pass_wall_ns", "round_wall_ns", "run_wall_ns",
+                   "passes", "grid_rounds", "one_block_runs")
 
 
 def kairos_last_stream_profile(g):

@@ -1196,15 +1196,16 @@ int32_t kairos_last_round_profile(const kairos_graph *g, int32_t max_rounds, uin
     return r;
 }
 
-int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out17) {
-    if (!g || !out17) return 0;
+int32_t kairos_last_stream_profile(const kairos_graph *g, uint64_t *out23) {
+    if (!g || !out23) return 0;
     const StreamCtr &c = g->last_sctr;
-    const uint64_t v[17] = {c.blocks, c.fix_rounds, c.fix_vertices, c.fix_edges, c.cand, c.scanned,
+    const uint64_t v[23] = {c.blocks, c.fix_rounds, c.fix_vertices, c.fix_edges, c.cand, c.scanned,
                             c.phase_cycles[0], c.phase_cycles[1], c.phase_cycles[2], c.phase_cycles[3],
                             c.cand_lanes[0], c.cand_lanes[1], c.cand_lanes[2], c.cand_lanes[3], c.cand_pairs,
-                            c.cand_improving, c.lanes_lowered};
-    for (int i = 0; i < 17; ++i) out17[i] = v[i];
-    return 17;
+                            c.cand_improving, c.lanes_lowered, c.wall_ns[0], c.wall_ns[1], c.wall_ns[2],
+                            c.segments[0], c.segments[1], c.segments[2]};
+    for (int i = 0; i < 23; ++i) out23[i] = v[i];
+    return 23;
 }
 
 int32_t kairos_last_phase_cycles(const kairos_graph *g, uint64_t *cycles8) {

@@ -239,6 +239,8 @@ struct StreamCtr {
     // 17-64), and candidate lanes in all
     unsigned long long cand_lanes[4];
     unsigned long long cand_pairs;
+    unsigned long long wall_ns[3];   // block 0's wall time in passes, grid-wide fix-up rounds and
+    unsigned long long segments[3];  // one-block runs (with their grid barriers), and their counts
     unsigned long long cand_improving;  // candidates (pass and fix-ups) that lowered some label
     unsigned long long lanes_lowered;   // labels lowered
     // SM cycles summed over warps when StreamArgs::phase_clock is set: 0 block passes (reading

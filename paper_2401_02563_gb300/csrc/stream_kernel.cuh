@@ -131,6 +131,18 @@ __device__ __forceinline__ void reached_add(unsigned long long *p, uint32_t lane
     }
 }
 
+constexpr int ST_CAND = ST_THREADS * ST_KE;  // candidates of one block tile
+
+// Candidate edges (records, or a fix-up vertex's edges, that passed the bounds): the block's
+// pass tile pools them in one list; a fix-up warp uses its own slice of 32 * ST_KE entries.
+// Once a pass candidate is relaxed, its slot holds the outcome instead: cm = the lanes reached
+// for the first time, t = flags (1: some label dropped, 2: the head joins the fix-ups).
+struct StreamCand {
+    unsigned long long cm[ST_CAND];  // lanes in which the edge may improve its head
+    int32_t u[ST_CAND], v[ST_CAND];
+    uint32_t t[ST_CAND], tau[ST_CAND];
+};
+
 // Relax up to G edges g < cnt (into head v[g], departure t[g], arrival tau[g]) in every lane,
 // given each edge's tail thresholds thr[g][.] and on[g] (bit i: this thread's lane lane + 32 i is
 // a candidate lane of the edge); the warp takes part as a whole.  With PRE the head labels
@@ -144,7 +156,8 @@ template <int W, bool PASS, bool PRE, bool D, int G = ST_G>
 __device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLaneReg<W> &R, int lane, int cnt,
                                             const uint32_t (&thr)[G][W / 32], const uint32_t (&hv)[G][W / 32],
                                             const int32_t (&v)[G], const uint32_t (&t)[G], const uint32_t (&tau)[G],
-                                            const unsigned (&on)[G], uint32_t tend, int32_t *fq, unsigned *fcount) {
+                                            const unsigned (&on)[G], uint32_t tend, int32_t *fq, unsigned *fcount,
+                                            StreamCand *L = nullptr, int base = 0) {
     constexpr int LPT = W / 32;
     bool adm[G][LPT];
     unsigned anyg = 0;
@@ -158,94 +171,112 @@ __device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLan
         }
         if (__any_sync(SFULL, any)) anyg |= 1u << g;
     }
-    if (!anyg) return;
-    uint32_t c[G][LPT];  // head labels: may be stale, never below the label
+    uint32_t fh[G][LPT];  // per edge the lanes reached for the first time, by half
+    unsigned dmask = 0;   // edges that lowered some label
+    if (anyg) {
+        uint32_t c[G][LPT];  // head labels: may be stale, never below the label
 #pragma unroll
-    for (int g = 0; g < G; ++g)
+        for (int g = 0; g < G; ++g)
 #pragma unroll
-        for (int i = 0; i < LPT; ++i)
-            c[g][i] = !adm[g][i] ? 0u : PRE ? hv[g][i] : __ldcg(a.arr + (size_t)v[g] * W + lane + 32 * i);
-    // lower the labels; per edge g the lanes reached for the first time, by half
-    uint32_t fh[G][LPT];
-    unsigned dmask = 0;  // edges that lowered some label
+            for (int i = 0; i < LPT; ++i)
+                c[g][i] = !adm[g][i] ? 0u : PRE ? hv[g][i] : __ldcg(a.arr + (size_t)v[g] * W + lane + 32 * i);
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-        bool imp = false;
+        for (int g = 0; g < G; ++g) {
+            bool imp = false;
 #pragma unroll
-        for (int i = 0; i < LPT; ++i) {
-            const bool d = adm[g][i] && tau[g] < c[g][i];
-            if (d) {
-                atomicMin(a.arr + (size_t)v[g] * W + lane + 32 * i, tau[g]);  // a reduction: result unused
-                if (D) atomicAdd(&diag_counts()[6], 1ull);  // diagnostics
-                imp = true;
+            for (int i = 0; i < LPT; ++i) {
+                const bool d = adm[g][i] && tau[g] < c[g][i];
+                if (d) {
+                    atomicMin(a.arr + (size_t)v[g] * W + lane + 32 * i, tau[g]);  // a reduction: result unused
+                    if (D) atomicAdd(&diag_counts()[6], 1ull);  // diagnostics
+                    imp = true;
+                }
+                fh[g][i] = __ballot_sync(SFULL, d && c[g][i] == INF);
             }
-            fh[g][i] = __ballot_sync(SFULL, d && c[g][i] == INF);
+            if (__any_sync(SFULL, imp)) dmask |= 1u << g;
         }
-        if (__any_sync(SFULL, imp)) dmask |= 1u << g;
+    } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int i = 0; i < LPT; ++i) fh[g][i] = 0u;
     }
-    if (!dmask) return;
-    if (D && lane == 0) atomicAdd(&diag_counts()[5], (unsigned long long)__popc(dmask));  // diagnostics
+    if (D && lane == 0 && dmask) atomicAdd(&diag_counts()[5], (unsigned long long)__popc(dmask));  // diagnostics
+    if (!PASS && !dmask) return;
+    // lane g takes edge g's outcome
+    int32_t vg = v[0];
+    uint32_t tg = tau[0], f0 = fh[0][0], f1 = LPT > 1 ? fh[0][LPT - 1] : 0u;
+#pragma unroll
+    for (int g = 1; g < G; ++g)
+        if (lane == g) {
+            vg = v[g];
+            tg = tau[g];
+            f0 = fh[g][0];
+            f1 = LPT > 1 ? fh[g][LPT - 1] : 0u;
+        }
+    const bool dropped = lane < G && ((dmask >> lane) & 1u);
+    if (PASS) {
+        // a pass leaves the outcome in the candidate's slot; the block applies the outcomes of
+        // the whole tile together after it (the summaries may lag, and the fix-up queue is taken
+        // only after the grid barrier that ends the pass)
+        if (lane < cnt) {
+            L->cm[base + lane] = ((unsigned long long)f1 << 32) | f0;
+            L->t[base + lane] = dropped ? (1u | (tg < tend ? 2u : 0u)) : 0u;
+        }
+        return;
+    }
     __syncwarp();  // the lanes' lowered labels precede the queue entries (below)
     // head summaries and fix-up queue: lane g for edge g, the edges' atomics in flight together
-    if (lane < G && ((dmask >> lane) & 1u)) {
-        int32_t vg = v[0];
-        uint32_t tg = tau[0], f0 = fh[0][0], f1 = LPT > 1 ? fh[0][LPT - 1] : 0u;
-#pragma unroll
-        for (int g = 1; g < G; ++g)
-            if (lane == g) {
-                vg = v[g];
-                tg = tau[g];
-                f0 = fh[g][0];
-                f1 = LPT > 1 ? fh[g][LPT - 1] : 0u;
-            }
+    if (dropped) {
         if (f0) reached_add(&a.rsum[2 * (size_t)vg], f0, tg);
         if (f1) reached_add(&a.rsum[2 * (size_t)vg + 1], f1, tg);
         atomicMin(&a.minrow[vg], tg);
         if (tg < tend) {
-            // a fix-up's queue entry is taken in the same round by a warp that then reads the
-            // labels; a pass's entries only after the grid barrier that ends the pass
-            if (!PASS) __threadfence();
+            // a fix-up's queue entry is taken in the same round by a warp that then reads the labels
+            __threadfence();
             const uint32_t bit = 1u << (vg & 31);
             if (!(atomicOr(&a.fbm[vg >> 5], bit) & bit)) fq[atomicAdd(fcount, 1u)] = vg;
         }
     }
 }
 
-// First index i in [0, deg) with tl[i] >= key (deg if none): 32 pivots per step, one per
-// thread, then the last 32 candidates.  Warp-uniform arguments and result.
-__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t *__restrict__ tl, uint32_t deg, uint32_t key,
-                                                     int lane) {
-    uint32_t lo = 0, hi = deg;  // A[i] < key for i < lo; hi = deg or A[hi] >= key
-    while (hi - lo > 32) {
-        const uint32_t span = hi - lo;
-        const uint32_t p = lo + (uint32_t)(((uint64_t)span * (uint32_t)(lane + 1)) >> 5) - 1u;  // lane 31: hi - 1
-        const bool below = __ldg(&tl[p]) < key;
-        const unsigned b = __ballot_sync(SFULL, below);
-        const int c = __popc(b);  // pivots below the key form a prefix
-        const uint32_t nlo = c ? __shfl_sync(SFULL, p, c - 1) + 1u : lo;
-        const uint32_t nhi = c < 32 ? __shfl_sync(SFULL, p, c < 32 ? c : 31) : hi;
-        lo = nlo;
-        hi = nhi;
+// First indices r0, r1 in [0, deg) with tl[r] >= k0, k1 (deg if none), tl ascending: per step
+// 32 pivots per search, one per thread, then the last 32 candidates.  The two searches' pivot
+// loads go out together, so their dependent chains overlap.  Warp-uniform arguments and results.
+__device__ __forceinline__ void warp_lower_bound2(const uint32_t *__restrict__ tl, uint32_t deg, uint32_t k0,
+                                                  uint32_t k1, int lane, uint32_t &r0, uint32_t &r1) {
+    uint32_t lo[2] = {0, 0}, hi[2] = {deg, deg};
+    const uint32_t key[2] = {k0, k1};
+    while (hi[0] - lo[0] > 32 || hi[1] - lo[1] > 32) {
+        uint32_t p[2];
+        bool below[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const uint32_t span = hi[s] - lo[s];
+            p[s] = span > 32 ? lo[s] + (uint32_t)(((uint64_t)span * (uint32_t)(lane + 1)) >> 5) - 1u : 0u;
+            below[s] = span > 32 && __ldg(&tl[p[s]]) < key[s];
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (hi[s] - lo[s] <= 32) continue;  // warp-uniform
+            const int c = __popc(__ballot_sync(SFULL, below[s]));  // pivots below the key form a prefix
+            const uint32_t nlo = c ? __shfl_sync(SFULL, p[s], c - 1) + 1u : lo[s];
+            const uint32_t nhi = c < 32 ? __shfl_sync(SFULL, p[s], c < 32 ? c : 31) : hi[s];
+            lo[s] = nlo;
+            hi[s] = nhi;
+        }
     }
-    const bool below = lo + (uint32_t)lane < hi && __ldg(&tl[lo + lane]) < key;
-    return lo + (uint32_t)__popc(__ballot_sync(SFULL, below));
+    bool below[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) below[s] = lo[s] + (uint32_t)lane < hi[s] && __ldg(&tl[lo[s] + lane]) < key[s];
+    r0 = lo[0] + (uint32_t)__popc(__ballot_sync(SFULL, below[0]));
+    r1 = lo[1] + (uint32_t)__popc(__ballot_sync(SFULL, below[1]));
 }
-
-// Candidate edges of one warp's tile (the records, or a fix-up vertex's edges, that passed
-// both bounds).
-constexpr int ST_CAND = ST_THREADS * ST_KE;  // candidates of one block tile
-
-// Candidate edges (records, or a fix-up vertex's edges, that passed the bounds): the block's
-// pass tile pools them in one list; a fix-up warp uses its own slice of 32 * ST_KE entries.
-struct StreamCand {
-    unsigned long long cm[ST_CAND];  // lanes in which the edge may improve its head
-    int32_t u[ST_CAND], v[ST_CAND];
-    uint32_t t[ST_CAND], tau[ST_CAND];
-};
 
 struct StreamSmem {
     int flag;
     unsigned F;              // the current fix-up frontier length (read by thread 0)
+    unsigned long long wt;   // diagnostics: block 0's last segment end (ns)
     unsigned next_tile;      // the block's next pass tile
     unsigned bcount[2];      // pooled candidates of the current block tile (by tile parity)
     uint32_t tile[32 * 65];  // readout transpose: 32 vertices x up to 64 lanes (+1 pad)
@@ -297,8 +328,8 @@ __device__ __forceinline__ void fix_vertex(const StreamArgs &a, const StreamLane
     const uint32_t deg = (uint32_t)(__ldg(&a.off[u + 1]) - o0);
     // departures before the block were relaxed in every lane usable then, and a label that
     // dropped during the block is at least its first departure
-    const uint32_t b0 = warp_lower_bound(a.t + o0, deg, max(tmin, tbeg), lane);
-    const uint32_t b1 = warp_lower_bound(a.t + o0, deg, tend, lane);
+    uint32_t b0, b1;
+    warp_lower_bound2(a.t + o0, deg, max(tmin, tbeg), tend, lane, b0, b1);
     uint32_t thr[ST_G][LPT];
 #pragma unroll
     for (int g = 0; g < ST_G; ++g)
@@ -414,6 +445,17 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
             ph_last = now;
         }
     };
+    // diagnostics: block 0's wall time by kind of segment (0 passes, 1 grid-wide fix-up rounds,
+    // 2 one-block runs), each ending at a grid barrier
+    auto wall = [&](int kind) {
+        if (D && tid == 0) {
+            const unsigned long long now = globaltimer();
+            C->wall_ns[kind] += now - S.wt;
+            C->segments[kind] += 1;
+            S.wt = now;
+        }
+    };
+    if (D && tid == 0) S.wt = globaltimer();
     mark(2);
     for (int k = a.k_begin; k < a.k_end; ++k) {
         const uint64_t lo = a.bnd[k], hi = a.bnd[k + 1];
@@ -523,7 +565,24 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                             const uint32_t x = thr[g][i];
                             thr[g][i] = (R.on[i] && x != INF) ? x + ((on[g] >> (2 + i)) & 1u) : INF;
                         }
-                    relax_batch<W, true, true, D, G>(a, R, lane, cnt, thr, hv, v, t, tau, on, tend, fq, fcount);
+                    relax_batch<W, true, true, D, G>(a, R, lane, cnt, thr, hv, v, t, tau, on, tend, fq, fcount, &L,
+                                                     base);
+                }
+                __syncthreads();
+                // the tile's outcomes, a candidate per thread: reached-lane words, minrow, queue
+                for (int i = threadIdx.x; i < len; i += ST_THREADS) {
+                    const uint32_t fl = L.t[i];
+                    if (!(fl & 1u)) continue;
+                    const int32_t vg = L.v[i];
+                    const uint32_t tg = L.tau[i];
+                    const unsigned long long fb = L.cm[i];
+                    if ((uint32_t)fb) reached_add(&a.rsum[2 * (size_t)vg], (uint32_t)fb, tg);
+                    if (fb >> 32) reached_add(&a.rsum[2 * (size_t)vg + 1], (uint32_t)(fb >> 32), tg);
+                    atomicMin(&a.minrow[vg], tg);
+                    if (fl & 2u) {
+                        const uint32_t bit = 1u << (vg & 31);
+                        if (!(atomicOr(&a.fbm[vg >> 5], bit) & bit)) fq[atomicAdd(fcount, 1u)] = vg;
+                    }
                 }
                 mark(3);
                 __syncthreads();  // the list is rewritten by the next tile
@@ -538,6 +597,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
             return;
         }
         mark(2);
+        wall(0);
         ++gen;  // the pass's queue is the first fix-up frontier
         // ---- fix-ups: frontier rounds over the block's departures ----
         for (unsigned round = 0;; ++round) {
@@ -605,6 +665,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                     return;
                 }
                 mark(2);
+                wall(2);
                 gen = __ldcg(&C->gen_shared[runs & 1]);
                 round = __ldcg(&C->round_shared[runs & 1]) - 1;  // the loop adds one
                 ++runs;
@@ -628,6 +689,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                 return;
             }
             mark(2);
+            wall(1);
             ++gen;
         }
     }
