@@ -324,6 +324,8 @@ kairos_status ensure_time_stream(kairos_graph *g, bool fwd, bool rev) {
             kairos_status st = cut_time_blocks(g->A, g->stream, g->m, eb, &ts);
             if (st != KAIROS_OK) return st;
         }
+        kairos_status st = build_vertex_spans(g->A, g->stream, g->n, c, &ts);
+        if (st != KAIROS_OK) return st;
     }
     return KAIROS_OK;
 }
@@ -489,6 +491,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
             a.rec = ts.rec;
             a.bnd = ts.bnd;
             a.bt = ts.bt;
+            a.span = ts.span;
             a.k_begin = kb;
             a.k_end = ke;
             a.off = csr.off;
@@ -938,7 +941,8 @@ kairos_status kairos_graph_get_info(const kairos_graph *g, kairos_graph_info *in
     const int64_t per_dir = (g->n + 1) * 8 + g->m * (8 + (g->lam_bits == 16 ? 2 : 4));
     info->device_bytes = per_dir * (g->has_rev ? 2 : 1) + (g->fwd.n_fence + g->rev.n_fence) * 4 +
                          (g->fwd.fidx ? g->n * 4 : 0) + (g->rev.fidx ? g->n * 4 : 0) + (int64_t)g->work.bytes +
-                         (g->ts_fwd.rec ? g->m * 16 : 0) + (g->ts_rev.rec ? g->m * 16 : 0) + (int64_t)g->sw[0].bytes +
+                         (g->ts_fwd.rec ? g->m * 16 : 0) + (g->ts_rev.rec ? g->m * 16 : 0) +
+                         (g->ts_fwd.span ? g->n * 8 : 0) + (g->ts_rev.span ? g->n * 8 : 0) + (int64_t)g->sw[0].bytes +
                          (int64_t)g->sw[1].bytes;
     info->build_ms = g->build_ms;
     info->index_ms = g->index_ms;

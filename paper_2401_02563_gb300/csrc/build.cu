@@ -731,7 +731,24 @@ kairos_status build_time_stream(const Allocator &A, cudaStream_t s, int64_t n, i
     return KAIROS_OK;
 }
 
+__global__ void vertex_spans(int64_t n, const uint64_t *off, const uint32_t *t, uint64_t *span) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = off[v], b = off[v + 1];
+        span[v] = a < b ? ((uint64_t)t[a] << 32) | t[b - 1] : ((uint64_t)INF << 32);
+    }
+}
+
+kairos_status build_vertex_spans(const Allocator &A, cudaStream_t s, int64_t n, const Csr &c, TimeStream *ts) {
+    if (ts->span) return KAIROS_OK;
+    ts->span = (uint64_t *)A.get((size_t)std::max<int64_t>(n, 1) * 8);
+    if (!ts->span) return fail(KAIROS_ERR_OOM, "time stream: device allocation failed");
+    if (n > 0) vertex_spans<<<grid_for(n, 256), 256, 0, s>>>(n, c.off, c.t, ts->span);
+    KAIROS_CUDA(cudaGetLastError(), "time stream: vertex spans");
+    return KAIROS_OK;
+}
+
 void free_time_stream(const Allocator &A, TimeStream *ts) {
+    A.put(ts->span);
     A.put(ts->rec);
     A.put(ts->bnd);
     A.put(ts->bt);

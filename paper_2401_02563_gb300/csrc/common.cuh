@@ -200,6 +200,8 @@ struct TimeStream {
     int32_t nblk = 0;
     int64_t block_edges = 0;   // target records per block the cut was made for
     uint32_t *bt_host = nullptr;  // host copy of bt
+    uint64_t *span = nullptr;  // [n] (first departure << 32) | last departure of each vertex's
+                               // list (INF << 32 | 0 for an empty list)
 };
 
 enum : int { KERR_FIX_ROUNDS = 5 };
@@ -255,6 +257,7 @@ struct StreamArgs {
     const StreamRec *rec;
     const uint64_t *bnd;
     const uint32_t *bt;
+    const uint64_t *span;      // [n] first and last departure of each vertex (TimeStream::span)
     int32_t k_begin, k_end;  // blocks swept
     // the same direction as a time-sorted CSR (fix-ups walk one vertex's list)
     const uint64_t *off;
@@ -291,6 +294,8 @@ int stream_max_blocks_w(int lam_bits);
 kairos_status build_time_stream(const Allocator &A, cudaStream_t s, int64_t n, int64_t m, const Csr &c, int lam_bits,
                                 StreamRec *out);
 kairos_status cut_time_blocks(const Allocator &A, cudaStream_t s, int64_t m, int64_t block_edges, TimeStream *ts);
+// The first and last departure of every vertex's time-sorted list.
+kairos_status build_vertex_spans(const Allocator &A, cudaStream_t s, int64_t n, const Csr &c, TimeStream *ts);
 void free_time_stream(const Allocator &A, TimeStream *ts);
 
 // Between resumable launches (serving): column operations on the [n][W] state.

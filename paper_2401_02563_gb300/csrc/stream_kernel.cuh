@@ -152,6 +152,14 @@ struct StreamCand {
 // arrival is earlier; then lane g updates head g's summaries: lanes reached for the first time
 // join its reached-lane word with the arrival as bound, minrow drops, and the head is queued for
 // this block's fix-ups when the arrival is below tend.
+// Whether vertex v, newly arrived at tau, has a departure in [tau, tend) (the only ones a fix-up
+// of the current block could take): its list's first departure is below tend and its last at
+// least tau.  A necessary condition, from one load; without it v is not queued.
+__device__ __forceinline__ bool may_continue(const StreamArgs &a, int32_t v, uint32_t tau, uint32_t tend) {
+    const uint64_t sp = __ldg(&a.span[v]);
+    return (uint32_t)(sp >> 32) < tend && (uint32_t)sp >= tau;
+}
+
 template <int W, bool PASS, bool PRE, bool D, int G = ST_G>
 __device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLaneReg<W> &R, int lane, int cnt,
                                             const uint32_t (&thr)[G][W / 32], const uint32_t (&hv)[G][W / 32],
@@ -231,7 +239,7 @@ __device__ __forceinline__ void relax_batch(const StreamArgs &a, const StreamLan
         if (f0) reached_add(&a.rsum[2 * (size_t)vg], f0, tg);
         if (f1) reached_add(&a.rsum[2 * (size_t)vg + 1], f1, tg);
         atomicMin(&a.minrow[vg], tg);
-        if (tg < tend) {
+        if (tg < tend && may_continue(a, vg, tg, tend)) {
             // a fix-up's queue entry is taken in the same round by a warp that then reads the labels
             __threadfence();
             const uint32_t bit = 1u << (vg & 31);
@@ -579,7 +587,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) stream_kernel(const StreamArgs 
                     if ((uint32_t)fb) reached_add(&a.rsum[2 * (size_t)vg], (uint32_t)fb, tg);
                     if (fb >> 32) reached_add(&a.rsum[2 * (size_t)vg + 1], (uint32_t)(fb >> 32), tg);
                     atomicMin(&a.minrow[vg], tg);
-                    if (fl & 2u) {
+                    if ((fl & 2u) && may_continue(a, vg, tg, tend)) {
                         const uint32_t bit = 1u << (vg & 31);
                         if (!(atomicOr(&a.fbm[vg >> 5], bit) & bit)) fq[atomicAdd(fcount, 1u)] = vg;
                     }
