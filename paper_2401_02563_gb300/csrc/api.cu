@@ -525,8 +525,37 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
     int bps = 0;
     int grid = stream_max_grid(lanes, g->lam_bits, g->sm_count, &bps);
     if (grid <= 0) return fail(KAIROS_ERR_CUDA, "stream edge-map: no resident launch shape (occupancy query failed)");
-    if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) grid = g->tuning.blocks_per_sm * g->sm_count;
-    else if (C >= 2) grid = std::max(1, bps / C) * g->sm_count;  // all launches in flight resident at once
+    // grid of each launch slot: with launches in flight the resident blocks per SM are shared out in
+    // proportion to each slot's time blocks (its sweep rounds), at least one each, so that the slot with
+    // the longer sweep is not left alone on a fraction of the GPU; all launches in flight stay resident
+    std::vector<int> slot_grid(C, grid);
+    if (g->tuning.blocks_per_sm > 0 && g->tuning.blocks_per_sm < bps) {
+        grid = g->tuning.blocks_per_sm * g->sm_count;
+        for (int k = 0; k < C; ++k) slot_grid[k] = grid;
+    } else if (C >= 2) {
+        grid = std::max(1, bps / C) * g->sm_count;
+        std::vector<double> cost(C, 0.0);
+        double total = 0;
+        for (size_t i = 0; i < plan.size(); ++i) {
+            const double c = 1.0 + (plan[i].a.k_end - plan[i].a.k_begin);
+            cost[i % C] += c;
+            total += c;
+        }
+        if (bps >= C) {
+            std::vector<int> b(C, 1);
+            int left = bps - C;
+            while (left > 0) {  // each remaining block to the slot with the most cost per block
+                int best = 0;
+                for (int k = 1; k < C; ++k)
+                    if (cost[k] / b[k] > cost[best] / b[best]) best = k;
+                ++b[best];
+                --left;
+            }
+            for (int k = 0; k < C; ++k) slot_grid[k] = b[k] * g->sm_count;
+        } else {
+            for (int k = 0; k < C; ++k) slot_grid[k] = grid;
+        }
+    }
 
     auto enqueue = [&](bool direct) -> kairos_status {
         if (C >= 2) {  // fork: the side streams start after everything before this call
@@ -538,7 +567,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
             const int slot = (int)(i % C);
             cudaStream_t si = slot ? g->sside[slot - 1] : s;
             KAIROS_CUDA(cudaMemsetAsync(plan[i].a.ctr, 0, sizeof(StreamCtr), si), "stream edge-map counters");
-            KAIROS_CUDA(stream_launch(plan[i].a, lanes, g->lam_bits, grid, si), "stream edge-map launch");
+            KAIROS_CUDA(stream_launch(plan[i].a, lanes, g->lam_bits, slot_grid[slot], si), "stream edge-map launch");
             if (direct && plan[i].host_out) {  // the copy engine, on the launch's stream
                 const std::vector<int> &q = plan[i].qid;
                 const uint32_t *src = g->sw[slot].stage;
@@ -560,7 +589,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
     bool launched = false;
     if (capturable) {
         std::string key("stream", 6);
-        key.append((const char *)&grid, sizeof(grid));
+        key.append((const char *)slot_grid.data(), slot_grid.size() * sizeof(int));
         for (const StreamPlanned &P : plan) key.append((const char *)&P.a, sizeof(StreamArgs));
         if (w.graph_exec && w.graph_key == key) {
             KAIROS_CUDA(cudaGraphLaunch(w.graph_exec, s), "graph launch");
