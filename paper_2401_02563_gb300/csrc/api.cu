@@ -557,7 +557,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
         }
     }
 
-    auto enqueue = [&](bool direct) -> kairos_status {
+    auto enqueue = [&]() -> kairos_status {
         if (C >= 2) {  // fork: the side streams start after everything before this call
             KAIROS_CUDA(cudaEventRecord(g->sfork, s), "concurrent launches: fork");
             for (int k = 0; k + 1 < C; ++k)
@@ -568,7 +568,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
             cudaStream_t si = slot ? g->sside[slot - 1] : s;
             KAIROS_CUDA(cudaMemsetAsync(plan[i].a.ctr, 0, sizeof(StreamCtr), si), "stream edge-map counters");
             KAIROS_CUDA(stream_launch(plan[i].a, lanes, g->lam_bits, slot_grid[slot], si), "stream edge-map launch");
-            if (direct && plan[i].host_out) {  // the copy engine, on the launch's stream
+            if (plan[i].host_out) {  // the copy engine, on the launch's stream
                 const std::vector<int> &q = plan[i].qid;
                 const uint32_t *src = g->sw[slot].stage;
                 for (size_t j = 0; j < q.size(); ++j)
@@ -585,12 +585,19 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
     };
 
     KAIROS_CUDA(cudaEventRecord(w.ev0, s), "event record");
-    const bool capturable = dev && !staged && s != nullptr && !getenv("KAIROS_NO_GRAPH");
+    // device and page-locked outputs: the whole sequence (launches in flight on their streams, and
+    // for staged page-locked outputs the copies after each launch) is captured into a CUDA graph and
+    // replayed while the same call repeats; pageable outputs are copied by the host path
+    const bool capturable = dev && s != nullptr && !getenv("KAIROS_NO_GRAPH");
     bool launched = false;
     if (capturable) {
         std::string key("stream", 6);
         key.append((const char *)slot_grid.data(), slot_grid.size() * sizeof(int));
-        for (const StreamPlanned &P : plan) key.append((const char *)&P.a, sizeof(StreamArgs));
+        key.append((const char *)&host_out, sizeof(host_out));
+        for (const StreamPlanned &P : plan) {
+            key.append((const char *)&P.a, sizeof(StreamArgs));
+            key.append((const char *)P.qid.data(), P.qid.size() * sizeof(int));
+        }
         if (w.graph_exec && w.graph_key == key) {
             KAIROS_CUDA(cudaGraphLaunch(w.graph_exec, s), "graph launch");
             launched = true;
@@ -599,7 +606,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
             drop_graph(g);
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                const kairos_status est = enqueue(false);
+                const kairos_status est = enqueue();
                 const cudaError_t ce = cudaStreamEndCapture(s, &graph);
                 if (est == KAIROS_OK && ce == cudaSuccess && graph &&
                     cudaGraphInstantiate(&w.graph_exec, graph, 0) == cudaSuccess) {
@@ -614,7 +621,7 @@ kairos_status run_stream_queries(kairos_graph *g, const kairos_query *qs, int32_
         }
     }
     if (!launched) {
-        st = enqueue(true);
+        st = enqueue();
         if (st != KAIROS_OK) return st;
     }
     KAIROS_CUDA(cudaEventRecord(w.ev1, s), "event record");

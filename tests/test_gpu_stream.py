@@ -220,9 +220,10 @@ def test_stream_mode_medium_full_size_certified():
 
 @pytest.mark.parametrize("shape", [dict(lanes=1, relax_mode=0), dict(lanes=16, relax_mode=0, concurrent=2),
                                    dict(lanes=64, relax_mode=3, concurrent=2)])
-def test_page_locked_host_outputs_are_written_directly(tiny, shape):
-    """Outputs in page-locked host memory are written by the kernels through their device
-    mapping (no staging copy): the same labels as the oracle, in one call or repeated."""
+def test_page_locked_host_outputs(tiny, shape):
+    """Outputs in page-locked host memory: written by the kernels through their device mapping
+    with one launch in flight, staged and moved by the copy engine (inside the captured graph)
+    with two; the same labels as the oracle, in one call or repeated (graph replay)."""
     el, orc, g = tiny
     g.set_tuning(**shape)
     qs = mixed_queries(el, 70, 0xB800)
