@@ -222,7 +222,6 @@ struct StreamCtr {
     int err;
     unsigned int pad0[29];
     PaddedU32 fcount[3];  // fix-up queue lengths, by generation mod 3
-    PaddedU32 fnext[3];   // fix-up vertices claimed, by generation mod 3
     PaddedU32 claim[2];   // pass tiles claimed past the first gridDim.x, by time block parity
     unsigned long long scanned;     // stream records read plus fix-up edges read
     unsigned long long cand;        // records whose lanes were examined
